@@ -1,0 +1,134 @@
+"""ORACLE -- test infrastructure only. Low-rank kernel approximations and the saddle-point
+preconditioner, dense FP64 (Secs. 4 and 5).
+
+* pivoted_cholesky: Algorithm 2 (greedy pivoted Cholesky of rank k, outer-product form),
+  in place on a dense copy of K. Reading C-13: ties go to the lowest index, and the loop also
+  stops once the largest residual diagonal is <= err_tol * max(diag K) (Table 1: err_tol = 1e-5).
+* nystrom: K ~ (K Q)(Q^T K Q)^{-1}(K Q)^T (Sec. 4), with the core factored as L D L^T and diagonal
+  entries below a threshold replaced by that threshold (reading C-16: 1e-10 * max D).
+* woodbury_apply: A^ = Theta + Y Z^T Z Y and A^{-1} = Theta^{-1} - Theta^{-1} Y Z^T
+  (I_k + Z Y Theta^{-1} Y Z^T)^{-1} Z Y Theta^{-1} (Sec. 5).
+* saddle preconditioner: the paper's P = [[A^, 0], [-y^T, -1]] (Sec. 5), and the block-diagonal
+  SPD form blockdiag(A^, y^T A^{-1} y) used with MINRES (reading C-12).
+"""
+import numpy as np
+
+
+def pivoted_cholesky(K, k, err_tol=0.0):
+    """Algorithm 2 on a dense copy of K. Returns (L, piv): L is n x r with K ~ L L^T in the
+    ORIGINAL row order, piv the r pivot indices in the order they were chosen."""
+    A = np.array(K, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    perm = np.arange(n)
+    r = 0
+    dmax0 = float(np.max(np.diag(A))) if n else 0.0
+    for j in range(n):
+        diag = np.diag(A)[j:]
+        l = j + int(np.argmax(diag))          # first maximal entry: ties -> lowest position
+        if not (A[l, l] > 0 and r < k):
+            break
+        if A[l, l] <= err_tol * dmax0:
+            break
+        r += 1
+        # symmetric swap of rows/columns j and l
+        A[[j, l], :] = A[[l, j], :]
+        A[:, [j, l]] = A[:, [l, j]]
+        perm[[j, l]] = perm[[l, j]]
+        A[j, j] = np.sqrt(A[j, j])
+        A[j + 1:, j] = A[j + 1:, j] / A[j, j]
+        for i in range(j + 1, n):
+            A[i:, i] = A[i:, i] - A[i:, j] * A[i, j]
+        # keep the trailing block symmetric so its diagonal and later swaps stay consistent
+        A[j + 1:, j + 1:] = np.tril(A[j + 1:, j + 1:]) + np.tril(A[j + 1:, j + 1:], -1).T
+    Lp = np.tril(A[:, :r])
+    L = np.zeros((n, r))
+    L[perm, :] = Lp
+    return L, perm[:r].copy()
+
+
+def nystrom(K, Q, rel_threshold=1e-10):
+    """K ~ C W^+ C^T with C = K Q and W = Q^T K Q factored as L D L^T (D thresholded).
+
+    Returns a factor Zt (n x k) with K ~ Zt Zt^T."""
+    K = np.asarray(K, dtype=np.float64)
+    C = K @ Q
+    W = Q.T @ C
+    W = 0.5 * (W + W.T)
+    L, D = ldl_nopivot(W)
+    thr = rel_threshold * max(1e-300, float(np.max(np.abs(D))))
+    D = np.where(D < thr, thr, D)
+    # W^{-1} = L^{-T} D^{-1} L^{-1}  =>  C W^{-1} C^T = (C L^{-T} D^{-1/2})(...)^T
+    X = np.linalg.solve(L, C.T)            # L^{-1} C^T
+    Zt = (X / np.sqrt(D)[:, None]).T
+    return Zt
+
+
+def ldl_nopivot(W):
+    """W = L D L^T with unit lower-triangular L (no pivoting), FP64."""
+    n = W.shape[0]
+    L = np.eye(n)
+    D = np.zeros(n)
+    for j in range(n):
+        D[j] = W[j, j] - np.sum(L[j, :j] ** 2 * D[:j])
+        for i in range(j + 1, n):
+            piv = D[j] if D[j] != 0 else 1e-300
+            L[i, j] = (W[i, j] - np.sum(L[i, :j] * L[j, :j] * D[:j])) / piv
+    return L, D
+
+
+def nystrom_columns(K, idx, rel_threshold=1e-10):
+    """Classic Nystrom: Q = columns idx of the identity."""
+    n = K.shape[0]
+    Q = np.zeros((n, len(idx)))
+    Q[np.asarray(idx), np.arange(len(idx))] = 1.0
+    return nystrom(K, Q, rel_threshold)
+
+
+def nystrom_random(K, k, seed, rel_threshold=1e-10):
+    """Q = orth(K G) with Gaussian G (n x k), orthonormalised by a Householder QR."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((K.shape[0], k))
+    Q, _ = np.linalg.qr(K @ G)
+    return nystrom(K, Q, rel_threshold)
+
+
+def woodbury_apply(Zt, theta, y, g):
+    """A^{-1} g for A^ = Theta + Y Z^T Z Y, Z = Zt^T (k x n), by the Woodbury identity."""
+    Z = Zt.T
+    ti = 1.0 / theta
+    core = np.eye(Z.shape[0]) + (Z * (y * ti * y)[None, :]) @ Z.T
+    u = Z @ (y * ti * g)
+    return ti * g - ti * y * (Z.T @ np.linalg.solve(core, u))
+
+
+def dense_Ahat(Zt, theta, y):
+    return np.diag(theta) + (y[:, None] * (Zt @ Zt.T)) * y[None, :]
+
+
+def saddle_matrix(K, theta, y):
+    """The Newton matrix of eq. (Newton): [[Y K Y + Theta, -y], [-y^T, 0]]."""
+    n = y.size
+    A = np.zeros((n + 1, n + 1))
+    A[:n, :n] = (y[:, None] * K) * y[None, :] + np.diag(theta)
+    A[:n, n] = -y
+    A[n, :n] = -y
+    return A
+
+
+def triangular_preconditioner(Ahat, y):
+    """The paper's P = [[A^, 0], [-y^T, -1]] (Sec. 5)."""
+    n = y.size
+    P = np.zeros((n + 1, n + 1))
+    P[:n, :n] = Ahat
+    P[n, :n] = -y
+    P[n, n] = -1.0
+    return P
+
+
+def blockdiag_apply(Zt, theta, y, g, s):
+    """MINRES preconditioner blockdiag(A^, s)^{-1} g with s = y^T A^{-1} y (reading C-12)."""
+    n = y.size
+    out = np.empty(n + 1)
+    out[:n] = woodbury_apply(Zt, theta, y, g[:n])
+    out[n] = g[n] / s
+    return out
