@@ -1,0 +1,357 @@
+"""Benchmark of the ANOVA-NFFT matvec (arXiv 2312.00538, Sec. 3) on the 1e6-point workload.
+
+Workload: n = 1,000,000 points, d = 9 N(0,1) features min-max scaled into [-0.2, 0.2], three
+3-D windows, sigma = 1, bandwidth N = 32 (oversampled grid 64^3), Kaiser-Bessel cut-off m = 4,
+FP32 plan, 1 right-hand side v ~ N(0,1). A step is one full matvec K v = sum_l K_l v (spread,
+reduce, FFT/scale/IFFT passes, interpolation, window sum) with v already resident in HBM; the
+plan (sort, tables) is built once before timing and reported separately. Between timed steps the
+L2 cache is flushed by writing a 512 MiB buffer (the matvec's working set, ~80 MB, fits in L2).
+
+`python bench.py --impl reference` times the FP64 CPU oracle (direct summation) on the host cores
+instead, on a bounded row sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ANOVA-NFFT matvec pts/s"
+UNIT = "pts/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128     # FP32 FMA units per Blackwell SM
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--sigma", type=float, default=1.0)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, seed_offset=0):
+    from synth import config2, matvec_vectors, SEED_BASE
+    cfg = config2(n=n, seed=SEED_BASE + 2 + seed_offset)
+    return cfg["X"], cfg["windows"], SEED_BASE + 2 + 100 + seed_offset
+
+
+def workload_name(n, sigma, nrhs):
+    return "anova_nfft_matvec n=%d d=9 windows=3x3D sigma=%g N=32 m=4 nrhs=%d" % (n, sigma, nrhs)
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while running (SM clock, max clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9 or parts[0] != self.gpu:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_rows_per_s(X, W, sigma, v, budget_s, max_rows, seed):
+    """Time the FP64 direct-sum oracle on a row sample sized to about budget_s seconds."""
+    from oracle import kernel as ok
+    from synth import subsample_rows
+    n = X.shape[0]
+    calib = subsample_rows(n, 16, seed)
+    t0 = time.perf_counter()
+    ok.anova_matvec(X, W, sigma, v, rows=calib)
+    t_row = (time.perf_counter() - t0) / len(calib)
+    rows = int(max(16, min(max_rows, budget_s / max(t_row, 1e-9))))
+    idx = subsample_rows(n, rows, seed + 1)
+    t0 = time.perf_counter()
+    ok.anova_matvec(X, W, sigma, v, rows=idx)
+    t = time.perf_counter() - t0
+    return rows / t, rows, t, ok.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.n
+    X, W, vseed = workload(n)
+    from synth import matvec_vectors
+    v = matvec_vectors(n, 1, vseed)[:, 0]
+    # size each step to ~4 s of CPU work so that warmup + steps end within a few minutes
+    rate0, rows0, _, cores = oracle_rows_per_s(X, W, args.sigma, v, 1.0, 20000, 7)
+    rows = int(max(16, min(20000, 4.0 * rate0)))
+    from oracle import kernel as ok
+    from synth import subsample_rows
+    for i in range(args.warmup):
+        ok.anova_matvec(X, W, args.sigma, v, rows=subsample_rows(n, rows, 100 + i))
+    times = []
+    for i in range(args.steps):
+        idx = subsample_rows(n, rows, 1000 + i)
+        t0 = time.perf_counter()
+        ok.anova_matvec(X, W, args.sigma, v, rows=idx)
+        times.append(time.perf_counter() - t0)
+    tot = float(np.sum(times))
+    value = rows * args.steps / tot
+    sample = ("FP64 direct sum of %d sampled output rows over all %d points and 3 windows per step "
+              "(a full matvec is n rows; pts/s = rows computed per second)" % (rows, n))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(n, args.sigma, 1), "oracle": "direct summation"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None when
+    the summary is missing or was taken on a different kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        entry = rec[kernel_key]
+        src = open(os.path.join(ROOT, entry["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != entry["source_sha256_16"]:
+            return None
+        return float(entry["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2312_00538_gb300 as ab
+    from synth import matvec_vectors
+
+    n, nrhs, sigma = args.n, args.nrhs, args.sigma
+    X, W, vseed = workload(n, seed_offset=rank)    # independent problem per rank (weak scaling)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = ab.anova_nfft_plan(X, W, sigma, N=32, m=4, flags=ab.ANOVA_FP32, stream=stream)
+    torch.cuda.synchronize()
+    plan_ms = 1000 * (time.perf_counter() - t0)
+    V = matvec_vectors(n, nrhs, vseed)
+    v = torch.tensor(np.ascontiguousarray(V.T), dtype=torch.float32, device="cuda")
+    if nrhs == 1:
+        v = v.reshape(-1)
+    Kv = torch.empty_like(v)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ab.anova_matvec(plan, v, Kv, nrhs)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ab.anova_plan_set_timing(plan, False)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s, e in ev:
+        flush.zero_()
+        s.record(stream)
+        step()
+        e.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = float(sum(s.elapsed_time(e) for s, e in ev))
+    _, launches = ab.anova_plan_stage_times(plan)
+    # same steps again with per-stage events, for the roofline of the dominant kernel
+    ab.anova_plan_set_timing(plan, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    stage_ms, _ = ab.anova_plan_stage_times(plan)
+    ab.anova_plan_set_timing(plan, False)
+    clocks = sampler.stop()
+
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * nrhs / (ms_per_step / 1000.0)
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.empty((nrhs, n), dtype=torch.float32, pin_memory=True)
+        vh.copy_(torch.from_numpy(np.ascontiguousarray(V.T).astype(np.float32)))
+        kh = torch.empty((nrhs, n), dtype=torch.float32, pin_memory=True)
+        for _ in range(2):
+            ab.anova_matvec_host(plan, vh, kh, nrhs)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ab.anova_matvec_host(plan, vh, kh, nrhs)
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * n * nrhs * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n * nrhs, "d2h_bytes_per_step": 4 * n * nrhs}
+
+    # ---------------------------------------------------------------- roofline
+    peaks, peak_kind = load_peaks()
+    P = W.shape[0]
+    m = 4
+    fma_per_pt = P * (2 * m) ** 3 * nrhs               # multiply-adds per point, one of spread/interp
+    dominant = "spread" if stage_ms["spread"] >= stage_ms["interp"] else "interp"
+    dom_ms = stage_ms[dominant] / args.steps
+    flops = 2.0 * fma_per_pt * n
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    traffic = profile_traffic("k_spread_f32_3d_m4" if dominant == "spread" else "k_interp_f32_3d_m4")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_tflops, "traffic": traffic,
+                "kernel": "k_%s (FP32, 3-D windows, m=4)" % dominant,
+                "peak_source": "derived: %d SMs x %d FP32 FMA/clk x 2 x %.0f MHz" % (
+                    SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ)}
+    alg_bytes = n * (P * 2 * 4 * 3 + 4 * nrhs + 4 * nrhs)   # coords read twice, v read, Kv written
+    hbm_gbs = alg_bytes / (ms_per_step / 1000.0) / 1e9
+    hbm = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": hbm_gbs,
+           "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
+           "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        vv = V[:, 0].astype(np.float64)
+        rate, rows, t, cores = oracle_rows_per_s(X, W, sigma, vv, 10.0, 20000, 5)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 direct sum of %d sampled output rows over all %d points (%.1f s); "
+                         "pts/s = output rows per second" % (rows, n, t)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(n, sigma, nrhs), "global_batch": world * n,
+                       "parallelism": "replicas (one independent problem per GPU)" if world > 1 else "single GPU",
+                       "l2": "flushed between steps (512 MiB write)", "plan_ms": plan_ms},
+            "gpu_launches": int(launches),
+            "stage_ms_per_step": {k: v2 / args.steps for k, v2 in stage_ms.items()},
+            "roofline": roofline,
+            "hbm_roofline": hbm,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

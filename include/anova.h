@@ -1,0 +1,189 @@
+/*
+ * anova.h -- C ABI of the GB300 ANOVA-NFFT kernel library.
+ *
+ * The library computes matrix-vector products with the extended Gaussian ANOVA kernel of
+ * arXiv 2312.00538 (Wagner, Pearson, Stoll), Sec. 3:
+ *
+ *     kappa(x_i, x_j) = sum_{l=1}^{P} eta_l exp(-||x_j^{W_l} - x_i^{W_l}||^2 / ell_l^2),
+ *     K v = K_1 v + ... + K_P v,
+ *
+ * each window W_l holding one to three features, and every K_l v evaluated by NFFT-based fast
+ * summation (Sec. 3: trigonometric-polynomial kernel of bandwidth N, adjoint NFFT, diagonal
+ * scaling by the Fourier coefficients, NFFT). On top of the matvec it provides the low-rank
+ * preconditioners of Sec. 4-5 and the interior point method of Sec. 2 (Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an anova_status; no C++ exception crosses this boundary. On an error
+ *    anova_last_error() returns a message for the calling thread; outputs are then unspecified.
+ *  - The caller owns every buffer it passes. Plans and preconditioners own the device memory
+ *    they allocate and release it in *_destroy.
+ *  - "device" pointers are CUDA global-memory addresses on the device that was current when the
+ *    plan was created; "host" pointers are ordinary CPU memory.
+ *  - Work is issued on the CUDA stream given at plan creation (NULL = the legacy default
+ *    stream). Calls returning device results are asynchronous with respect to the host unless
+ *    stated otherwise; synchronise that stream before reading them.
+ *  - Points must lie in [-0.2, 0.2] in every feature used by a window (the plan's fit interval
+ *    for kernel differences is |t| <= 0.4); otherwise ANOVA_ERR_OUT_OF_RANGE.
+ *
+ * A plan may be used from one host thread at a time.
+ */
+#ifndef ANOVA_H
+#define ANOVA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct anova_plan *anova_plan_t;
+typedef struct lowrank *lowrank_t;
+
+typedef enum {
+    ANOVA_OK = 0,
+    ANOVA_ERR_INVALID_ARG = 1,   /* a size, flag, pointer or parameter is not allowed */
+    ANOVA_ERR_OUT_OF_RANGE = 2,  /* a point coordinate lies outside [-0.2, 0.2] */
+    ANOVA_ERR_NONFINITE = 3,     /* an input holds NaN or Inf */
+    ANOVA_ERR_OOM = 4,           /* a device or host allocation failed */
+    ANOVA_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
+    ANOVA_ERR_NOT_CONVERGED = 6, /* an iteration hit its limit before its tolerance */
+    ANOVA_ERR_BREAKDOWN = 7,     /* a Krylov or factorisation step divided by zero */
+    ANOVA_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} anova_status;
+
+/* Plan precision flags (anova_nfft_plan `flags`). v and Kv use the same element type. */
+enum {
+    ANOVA_FP32 = 0, /* float spread / FFT / interpolation with float accumulation */
+    ANOVA_FP64 = 1  /* double everywhere (the "precise" plan) */
+};
+
+/* Low-rank preconditioner kinds (lowrank_precond_build `kind`). */
+enum {
+    PCHOL_GREEDY = 0, /* Algorithm 2: greedy pivoted Cholesky (Sec. 4) */
+    NYSTROM = 1       /* Nystrom K ~ (KQ)(Q^T K Q)^{-1}(KQ)^T with Q = pivoted columns (Sec. 4) */
+};
+
+/*
+ * anova_nfft_plan -- build the fast-summation plan for K = sum_l K_l (Sec. 3).
+ *
+ * points  host, n x d, row-major FP64: point i is points[i*d .. i*d+d-1].
+ * windows host, P x 3 int32, 0-based feature indices; a window of one or two features is padded
+ *         with -1 after its valid entries (Sec. 3: W_l holds at most three features).
+ * sigma   the kernel length scale ell of exp(-r^2/ell^2), shared by all windows; eta_l = 1.
+ * N       even bandwidth of the trigonometric polynomial (Sec. 3, N in 2N); 4 <= N <= 256.
+ * m       window cut-off of the NFFT (Sec. 3, O(m^d n)); the Kaiser-Bessel window covers 2m
+ *         grid points per dimension on an oversampled grid of n_os = 2N points.
+ *         FP32 plans accept 2 <= m <= 6, FP64 plans 3 <= m <= 8.
+ * flags   ANOVA_FP32 or ANOVA_FP64.
+ * cuda_stream  a cudaStream_t (or NULL) on which every later call of this plan is issued.
+ * out     receives the plan. The plan copies what it needs; `points` may be freed on return.
+ *
+ * Errors: INVALID_ARG (n < 1, d < 1, P < 1, bad window entries, N odd or out of range, m out of
+ * range, sigma not positive), NONFINITE, OUT_OF_RANGE, OOM, CUDA. Synchronises the stream.
+ */
+anova_status anova_nfft_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                             double sigma, int N, int m, int flags, void *cuda_stream,
+                             anova_plan_t *out);
+
+/*
+ * anova_nfft_plan_ex -- as anova_nfft_plan, with an individual length scale ell_l and weight
+ * eta_l per window (Sec. 3: "each kernel kappa_l is assigned an individual kernel parameter").
+ * ell: host, P positive values. eta: host, P finite values, or NULL for all ones.
+ */
+anova_status anova_nfft_plan_ex(const double *points, int64_t n, int d, const int32_t *windows,
+                                int P, const double *ell, const double *eta, int N, int m,
+                                int flags, void *cuda_stream, anova_plan_t *out);
+
+/*
+ * anova_matvec -- Kv = K v for nrhs right-hand sides (Sec. 3, K v = K_1 v + ... + K_P v).
+ *
+ * v   device, n x nrhs column-major (column r at v + r*n), element type of the plan.
+ * Kv  device, n x nrhs column-major, overwritten. Must not overlap v.
+ * nrhs >= 1. Asynchronous on the plan's stream. The first call with a larger nrhs than any
+ * earlier call enlarges the plan's workspace (a device allocation). Errors: INVALID_ARG, OOM,
+ * CUDA.
+ */
+anova_status anova_matvec(anova_plan_t plan, const void *v, void *Kv, int nrhs);
+
+/*
+ * anova_matvec_host -- as anova_matvec with HOST buffers: copies v to the device, runs the
+ * matvec and copies Kv back, then synchronises the plan's stream. Uses plan-owned staging
+ * buffers (pinned host memory is faster but not required).
+ */
+anova_status anova_matvec_host(anova_plan_t plan, const void *v_host, void *Kv_host, int nrhs);
+
+/*
+ * anova_window_matvec -- K_l v for the single window l (0 <= l < P) of the plan, nrhs = 1,
+ * device buffers of the plan's type (a stage of the same fast summation, for testing and for
+ * per-window low-rank factors, Sec. 4 "applied to each individual matrix").
+ */
+anova_status anova_window_matvec(anova_plan_t plan, int l, const void *v, void *Kv);
+
+/*
+ * Stage entry points of one window l (nrhs = 1, device buffers of the plan's type). The grid has
+ * n_os^{d_l} entries (n_os = 2N), row-major over the window's features in window order; grid
+ * index u in [0, n_os) sits at position u/n_os - 1/2.
+ *   anova_spread_grid : grid[u] = sum_i v_i prod_k psi(s_ik - u_k), s = (x + 1/2) n_os.
+ *   anova_conv_grid   : out = IDFT(D .* DFT(in)), unnormalised inverse, with
+ *                       D_J = eta_l prod_k b_{J_k} / Psi(J_k)^2 on J in I_N^{d_l}, 0 elsewhere.
+ *   anova_interp_grid : f_i = sum_u grid[u] prod_k psi(s_ik - u_k), f in original point order.
+ * psi is the Kaiser-Bessel window of cut-off m (normalised to psi(0) = 1) and Psi its Fourier
+ * transform; b the 1-D Fourier coefficients of the Gaussian (see anova_kernel_coeffs).
+ * anova_conv_grid reads every grid entry; the others touch only the footprint of the points.
+ */
+anova_status anova_spread_grid(anova_plan_t plan, int l, const void *v, void *grid);
+anova_status anova_conv_grid(anova_plan_t plan, int l, const void *grid_in, void *grid_out);
+anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void *f);
+
+/* Plan facts. Any output pointer may be NULL. device_bytes = device memory the plan holds. */
+anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
+                             int64_t *device_bytes);
+
+/*
+ * Per-stage timing of anova_matvec (CUDA events recorded on the plan's stream between the
+ * stages). Stages: ANOVA_STAGE_SPREAD (adjoint-NFFT spreading), ANOVA_STAGE_REDUCE (partial-tile
+ * reduction onto the grid), ANOVA_STAGE_FFT (FFT / scaling / inverse FFT passes),
+ * ANOVA_STAGE_INTERP (NFFT interpolation), ANOVA_STAGE_SUM (sum over windows).
+ * anova_plan_set_timing: turns recording on (enable != 0) or off and clears what was recorded.
+ * anova_plan_stage_times: synchronises the stream and returns in ms[ANOVA_NUM_STAGES] the total
+ *   milliseconds per stage since the last reset, and in *launches the number of kernels the plan
+ *   launched since then (counted whether or not timing is on). Either output may be NULL.
+ */
+enum {
+    ANOVA_STAGE_SPREAD = 0,
+    ANOVA_STAGE_REDUCE = 1,
+    ANOVA_STAGE_FFT = 2,
+    ANOVA_STAGE_INTERP = 3,
+    ANOVA_STAGE_SUM = 4,
+    ANOVA_NUM_STAGES = 5
+};
+anova_status anova_plan_set_timing(anova_plan_t plan, int enable);
+anova_status anova_plan_stage_times(anova_plan_t plan, double *ms, int64_t *launches);
+
+/* Release a plan and its device memory (NULL is ignored). Synchronises its stream. */
+void anova_plan_destroy(anova_plan_t plan);
+
+/*
+ * Host-only plan mathematics, exported so that they can be checked without a GPU.
+ *
+ * anova_kernel_coeffs: the 1-D Fourier coefficients b_0..b_{N/2-1} of the trigonometric
+ *   polynomial b_0 + 2 sum_{k>=1} b_k cos(2 pi k t) fitted (least squares, FP64) to
+ *   exp(-t^2/ell^2) on |t| <= 0.4; b_{-N/2} = 0 (Sec. 3, kappa~ with bandwidth N).
+ *   b: host, N/2 doubles.
+ * anova_window_hat: Psi(k) = int psi(t) cos(2 pi k t / n_os) dt for k = 0..count-1, the
+ *   transform of the normalised Kaiser-Bessel window of cut-off m on a grid of n_os points.
+ */
+anova_status anova_kernel_coeffs(double ell, int N, double *b);
+anova_status anova_window_hat(int m, int n_os, int count, double *Psi);
+
+/* Thread-local message of the last error of this thread ("" if none). Never NULL. */
+const char *anova_last_error(void);
+
+/* Library version string. */
+const char *anova_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANOVA_H */

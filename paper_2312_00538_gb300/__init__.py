@@ -1,0 +1,270 @@
+"""Python binding of the GB300 ANOVA-NFFT library (libanova.so, C ABI in include/anova.h).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels. Device buffers
+are torch CUDA tensors (their data pointers are passed through), host buffers NumPy arrays.
+The functions keep the C names. The library must have been built (``__graft_entry__.build()``
+or ``python paper_2312_00538_gb300/_build.py``); importing without it raises ImportError.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libanova.so")
+
+ANOVA_OK = 0
+ANOVA_ERR_INVALID_ARG = 1
+ANOVA_ERR_OUT_OF_RANGE = 2
+ANOVA_ERR_NONFINITE = 3
+ANOVA_ERR_OOM = 4
+ANOVA_ERR_CUDA = 5
+ANOVA_ERR_NOT_CONVERGED = 6
+ANOVA_ERR_BREAKDOWN = 7
+ANOVA_ERR_TIMEOUT = 8
+STATUS_NAMES = {0: "ANOVA_OK", 1: "ANOVA_ERR_INVALID_ARG", 2: "ANOVA_ERR_OUT_OF_RANGE",
+                3: "ANOVA_ERR_NONFINITE", 4: "ANOVA_ERR_OOM", 5: "ANOVA_ERR_CUDA",
+                6: "ANOVA_ERR_NOT_CONVERGED", 7: "ANOVA_ERR_BREAKDOWN", 8: "ANOVA_ERR_TIMEOUT"}
+
+ANOVA_FP32 = 0
+ANOVA_FP64 = 1
+PCHOL_GREEDY = 0
+NYSTROM = 1
+
+
+class AnovaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+
+_c_int = ctypes.c_int
+_c_i64 = ctypes.c_int64
+_c_dbl = ctypes.c_double
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lp = ctypes.POINTER(ctypes.c_int64)
+
+_SIGNATURES = {
+    "anova_nfft_plan": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _c_dbl, _c_int, _c_int, _c_int,
+                                 _vp, ctypes.POINTER(_vp)]),
+    "anova_nfft_plan_ex": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _dp, _dp, _c_int, _c_int,
+                                    _c_int, _vp, ctypes.POINTER(_vp)]),
+    "anova_matvec": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "anova_matvec_host": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "anova_window_matvec": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "anova_spread_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "anova_conv_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "anova_interp_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "anova_plan_info": (_c_int, [_vp, _lp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                 ctypes.POINTER(_c_int), _lp]),
+    "anova_plan_destroy": (None, [_vp]),
+    "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
+    "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
+    "anova_kernel_coeffs": (_c_int, [_c_dbl, _c_int, _dp]),
+    "anova_window_hat": (_c_int, [_c_int, _c_int, _c_int, _dp]),
+    "anova_last_error": (ctypes.c_char_p, []),
+    "anova_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library (ctypes.CDLL). Raises ImportError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libanova.so is not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return sorted(_SIGNATURES)
+
+
+def _check(status):
+    if status != ANOVA_OK:
+        raise AnovaError(status, lib().anova_last_error().decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _dev_ptr(t):
+    """Data pointer of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Owns an anova_plan_t; destroyed with the object (or by .destroy())."""
+
+    def __init__(self, handle, n, P, precision):
+        self.handle = handle
+        self.n = n
+        self.P = P
+        self.precision = precision
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == ANOVA_FP64 else torch.float32
+
+    def destroy(self):
+        if self.handle:
+            lib().anova_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def anova_nfft_plan(points, windows, sigma, N=32, m=4, flags=ANOVA_FP32, stream=None):
+    """anova_nfft_plan: points (n x d, host), windows (P x 3 int32, -1 padded)."""
+    X = _f64(points)
+    if X.ndim != 2:
+        raise ValueError("points must be n x d")
+    W = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 3)
+    h = _vp()
+    _check(lib().anova_nfft_plan(_ptr(X, ctypes.c_double), X.shape[0], X.shape[1],
+                                 _ptr(W, ctypes.c_int32), W.shape[0], float(sigma), int(N), int(m),
+                                 int(flags), _stream_handle(stream), ctypes.byref(h)))
+    return Plan(h, X.shape[0], W.shape[0], flags & 1)
+
+
+def anova_nfft_plan_ex(points, windows, ell, eta=None, N=32, m=4, flags=ANOVA_FP32, stream=None):
+    """anova_nfft_plan_ex: one length scale ell_l (and weight eta_l) per window."""
+    X = _f64(points)
+    W = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 3)
+    ell = _f64(np.broadcast_to(ell, (W.shape[0],)))
+    eta_p = None
+    if eta is not None:
+        eta = _f64(np.broadcast_to(eta, (W.shape[0],)))
+        eta_p = _ptr(eta, ctypes.c_double)
+    h = _vp()
+    _check(lib().anova_nfft_plan_ex(_ptr(X, ctypes.c_double), X.shape[0], X.shape[1],
+                                    _ptr(W, ctypes.c_int32), W.shape[0], _ptr(ell, ctypes.c_double),
+                                    eta_p, int(N), int(m), int(flags), _stream_handle(stream),
+                                    ctypes.byref(h)))
+    return Plan(h, X.shape[0], W.shape[0], flags & 1)
+
+
+def anova_matvec(plan, v, Kv, nrhs=1):
+    """anova_matvec: v, Kv device tensors holding n x nrhs column-major (i.e. shape (nrhs, n)
+    contiguous, or (n,) for one right-hand side)."""
+    _check(lib().anova_matvec(plan.handle, _dev_ptr(v), _dev_ptr(Kv), int(nrhs)))
+
+
+def _host_ptr(a, plan, nrhs):
+    if isinstance(a, np.ndarray):
+        dt = np.float64 if plan.precision == ANOVA_FP64 else np.float32
+        if a.dtype != dt or not (a.flags.f_contiguous or a.ndim == 1) or a.size != plan.n * nrhs:
+            raise ValueError("host buffers must be contiguous arrays of the plan's type")
+        return ctypes.c_void_p(a.ctypes.data)
+    # a torch CPU tensor (e.g. pinned): shape (nrhs, n) or (n,), contiguous
+    if a.device.type != "cpu" or not a.is_contiguous() or a.numel() != plan.n * nrhs:
+        raise ValueError("host buffers must be contiguous CPU tensors of n * nrhs elements")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def anova_matvec_host(plan, v, Kv, nrhs=1):
+    """anova_matvec_host: v, Kv host buffers (NumPy arrays in column-major order, or contiguous
+    torch CPU tensors of shape (nrhs, n)), n * nrhs elements of the plan's type."""
+    _check(lib().anova_matvec_host(plan.handle, _host_ptr(v, plan, nrhs), _host_ptr(Kv, plan, nrhs),
+                                   int(nrhs)))
+
+
+def anova_window_matvec(plan, l, v, Kv):
+    _check(lib().anova_window_matvec(plan.handle, int(l), _dev_ptr(v), _dev_ptr(Kv)))
+
+
+def anova_spread_grid(plan, l, v, grid):
+    _check(lib().anova_spread_grid(plan.handle, int(l), _dev_ptr(v), _dev_ptr(grid)))
+
+
+def anova_conv_grid(plan, l, grid_in, grid_out):
+    _check(lib().anova_conv_grid(plan.handle, int(l), _dev_ptr(grid_in), _dev_ptr(grid_out)))
+
+
+def anova_interp_grid(plan, l, grid, f):
+    _check(lib().anova_interp_grid(plan.handle, int(l), _dev_ptr(grid), _dev_ptr(f)))
+
+
+def anova_plan_info(plan):
+    n = ctypes.c_int64()
+    P = ctypes.c_int()
+    nos = ctypes.c_int()
+    fl = ctypes.c_int()
+    nb = ctypes.c_int64()
+    _check(lib().anova_plan_info(plan.handle, ctypes.byref(n), ctypes.byref(P), ctypes.byref(nos),
+                                 ctypes.byref(fl), ctypes.byref(nb)))
+    return dict(n=n.value, P=P.value, n_os=nos.value, flags=fl.value, device_bytes=nb.value)
+
+
+def anova_plan_destroy(plan):
+    plan.destroy()
+
+
+STAGES = ("spread", "reduce", "fft", "interp", "sum")
+
+
+def anova_plan_set_timing(plan, enable=True):
+    _check(lib().anova_plan_set_timing(plan.handle, 1 if enable else 0))
+
+
+def anova_plan_stage_times(plan):
+    """Returns (dict stage -> total ms since the last reset, kernel launches since then)."""
+    ms = np.zeros(len(STAGES))
+    launches = ctypes.c_int64()
+    _check(lib().anova_plan_stage_times(plan.handle, _ptr(ms, ctypes.c_double),
+                                        ctypes.byref(launches)))
+    return dict(zip(STAGES, ms.tolist())), launches.value
+
+
+def anova_kernel_coeffs(ell, N):
+    b = np.zeros(N // 2)
+    _check(lib().anova_kernel_coeffs(float(ell), int(N), _ptr(b, ctypes.c_double)))
+    return b
+
+
+def anova_window_hat(m, n_os, count):
+    out = np.zeros(count)
+    _check(lib().anova_window_hat(int(m), int(n_os), int(count), _ptr(out, ctypes.c_double)))
+    return out
+
+
+def anova_last_error():
+    return lib().anova_last_error().decode()
+
+
+def anova_version():
+    return lib().anova_version().decode()

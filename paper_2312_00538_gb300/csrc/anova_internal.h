@@ -1,0 +1,148 @@
+// Internal declarations of the ANOVA-NFFT library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/anova.h"
+
+namespace anova {
+
+// ----------------------------------------------------------------------------- fixed choices
+constexpr double kOversampling = 2.0;  // n_os = 2N
+constexpr double kEpsB = 0.1;          // kernel fit on |t| <= 1/2 - eps_B
+constexpr double kBoxHalf = 0.2;       // points in [-0.2, 0.2]
+constexpr int kSegMax = 256;           // points per segment (one cell, split at this size)
+constexpr int kWiMax = 2048;           // points per spread work item (one bin)
+constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
+constexpr int kMaxWindows = 64;
+
+// ----------------------------------------------------------------------------- host maths
+double kb_beta();
+double kb_window(double t, int m);
+bool kernel_coeffs(double ell, int N, std::vector<double> &b);
+void window_hat(int m, int n_os, int count, double *Psi);
+bool window_poly(int m, int deg, std::vector<double> &coef);
+bool deconv_diag(double ell, int N, int m, int n_os, std::vector<double> &D1);
+
+// ----------------------------------------------------------------------------- error state
+void set_error(const std::string &msg);
+anova_status fail(anova_status st, const std::string &msg);
+anova_status cuda_fail(cudaError_t e, const char *what);
+
+#define ANOVA_CUDA_TRY(call)                                             \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::anova::cuda_fail(_e, #call);     \
+    } while (0)
+
+// ----------------------------------------------------------------------------- plan layout
+struct WindowInfo {
+    int dw = 0;                 // number of features, 1..3
+    int feat[3] = {-1, -1, -1};
+    double ell = 1.0, eta = 1.0;
+    int seg_begin = 0, seg_end = 0;  // global segment range
+    int wi_begin = 0, wi_end = 0;    // global spread work-item range
+    int box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};  // grid box touched by footprints
+    int64_t grid_off = 0;            // element offset of this window's grid (one RHS)
+    int bin_off = 0;                 // offset of this window's bin table
+    int tile_begin[3] = {0, 0, 0}, tile_end[3] = {0, 0, 0};  // FFT tiles of each axis pass
+    int mb_begin = 0, mb_end = 0;    // bins split into several work items
+    int64_t box_volume() const {
+        int64_t v = 1;
+        for (int k = 0; k < dw; ++k) v *= (box_hi[k] - box_lo[k]);
+        return v;
+    }
+};
+
+// A group of consecutive windows with the same number of features (one launch per group).
+struct Group {
+    int dw = 0;
+    int w_begin = 0, w_end = 0;
+    int seg_begin = 0, seg_end = 0;
+    int wi_begin = 0, wi_end = 0;
+    int tiles_begin[3] = {0, 0, 0}, tiles_end[3] = {0, 0, 0};  // FFT tiles per pass
+};
+
+// Per-window constants of the device kernels (small; copied into a device table).
+struct DevWindow {
+    int dw;
+    int box_lo[3], box_hi[3];
+    long long grid_off;
+    int bin_off;
+    int pad;
+};
+
+}  // namespace anova
+
+struct anova_plan {
+    int64_t n = 0;
+    int d = 0, P = 0, N = 0, m = 0, n_os = 0, prec = 0;
+    int B = 4;          // bin edge in cells
+    int NB = 0;         // bins per dimension
+    int tile_w = 0;     // spread tile edge: B + 2m - 1
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<anova::WindowInfo> win;   // internal window order (grouped by dw)
+    std::vector<int> user_to_internal;    // user window index -> internal index
+    std::vector<anova::Group> groups;
+    int nseg = 0, nwi = 0, ntiles = 0;
+    int64_t grid_total = 0;               // elements of all windows' grids (one RHS)
+    std::vector<double> poly;             // window polynomial coefficients (FP32 kernels)
+
+    // device memory
+    void *frac = nullptr;         // T[3][P*n]: fractional cell offsets, sorted per window
+    int32_t *perm = nullptr;      // [P*n]: sorted position -> original point index
+    int4 *segs = nullptr;         // {cell packed, sorted start, count, window}
+    int4 *wis = nullptr;          // {window, seg_begin, seg_end, tile origin packed}
+    int2 *bins = nullptr;         // per window per bin: {first work item, count}
+    int4 *mbins = nullptr;        // multi-item bins: {first work item, count, tile volume, 0}
+    int nmbins = 0;
+    int4 *ftiles = nullptr;       // FFT tiles: {window, p, q0, pass}
+    anova::DevWindow *dwin = nullptr;
+    void *D1br = nullptr;         // T[P][3][n_os]: deconvolution diagonal per axis, bit-reversed
+    void *tw = nullptr;           // T[n_os]: twiddles (re, im) pairs for k < n_os/2
+    int64_t static_bytes = 0;
+
+    // workspace, grown on demand
+    int ws_rhs = 0;
+    void *grids = nullptr;        // T[4][ws_rhs][grid_total]
+    void *tiles = nullptr;        // T[nwi][ws_rhs][tile_vol]
+    void *part = nullptr;         // T[P][ws_rhs][n]
+    int64_t ws_bytes = 0;
+    // host-call staging
+    void *dv = nullptr, *dkv = nullptr;
+    int stage_rhs = 0;
+
+    // optional per-stage CUDA-event timing (anova_plan_set_timing)
+    struct StageEvt {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool timing = false;
+    std::vector<StageEvt> evts;
+    std::vector<cudaEvent_t> evt_pool;
+    int64_t launches = 0;          // kernels launched since the last timing reset
+};
+
+namespace anova {
+enum { STAGE_SPREAD = 0, STAGE_REDUCE = 1, STAGE_FFT = 2, STAGE_INTERP = 3, STAGE_SUM = 4, NUM_STAGES = 5 };
+// Records a CUDA event on the plan's stream when timing is on; returns the event (or null).
+cudaEvent_t stage_event(anova_plan *p);
+void stage_record(anova_plan *p, int stage, cudaEvent_t a, cudaEvent_t b);
+size_t elem_size(const anova_plan *p);
+anova_status ensure_workspace(anova_plan *p, int nrhs);
+// Runs the fast summation for `nrhs` columns (element type T). If only_window >= 0, only that
+// internal window contributes. Defined per precision in matvec_f32.cu / matvec_f64.cu.
+template <typename T>
+anova_status run_matvec_t(anova_plan *p, const void *v, void *Kv, int nrhs, int only_window);
+template <typename T>
+anova_status run_spread_grid_t(anova_plan *p, int w, const void *v, void *grid);
+template <typename T>
+anova_status run_conv_grid_t(anova_plan *p, int w, const void *in, void *out);
+template <typename T>
+anova_status run_interp_grid_t(anova_plan *p, int w, const void *grid, void *f);
+}  // namespace anova

@@ -1,0 +1,296 @@
+// Exported C ABI of the ANOVA-NFFT matvec (declarations and contracts in include/anova.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "anova_internal.h"
+
+namespace anova {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+anova_status fail(anova_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+anova_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return ANOVA_ERR_OOM;
+    return ANOVA_ERR_CUDA;
+}
+
+anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                         const double *ell, const double *eta, int N, int m, int flags,
+                         void *stream, anova_plan_t *out);
+void destroy_plan(anova_plan *p);
+
+// Runs a plan call on the plan's device, restoring the caller's current device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename F>
+anova_status guarded(F &&f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return fail(ANOVA_ERR_OOM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(ANOVA_ERR_INVALID_ARG, e.what());
+    } catch (...) {
+        return fail(ANOVA_ERR_INVALID_ARG, "unknown exception");
+    }
+}
+
+cudaEvent_t stage_event(anova_plan *p) {
+    if (!p->timing) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!p->evt_pool.empty()) {
+        e = p->evt_pool.back();
+        p->evt_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    if (cudaEventRecord(e, p->stream) != cudaSuccess) {
+        p->evt_pool.push_back(e);
+        return nullptr;
+    }
+    return e;
+}
+
+void stage_record(anova_plan *p, int stage, cudaEvent_t a, cudaEvent_t b) {
+    if (!p->timing || !a || !b) return;
+    p->evts.push_back({stage, a, b});
+}
+
+static void reset_timing(anova_plan *p) {
+    std::vector<cudaEvent_t> seen;
+    for (auto &x : p->evts) {
+        for (cudaEvent_t e : {x.a, x.b})
+            if (std::find(seen.begin(), seen.end(), e) == seen.end()) seen.push_back(e);
+    }
+    for (cudaEvent_t e : seen) p->evt_pool.push_back(e);
+    p->evts.clear();
+    p->launches = 0;
+}
+
+void release_timing(anova_plan *p) {
+    reset_timing(p);
+    for (cudaEvent_t e : p->evt_pool) cudaEventDestroy(e);
+    p->evt_pool.clear();
+}
+
+}  // namespace anova
+
+using namespace anova;
+
+extern "C" {
+
+anova_status anova_nfft_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                             double sigma, int N, int m, int flags, void *cuda_stream,
+                             anova_plan_t *out) {
+    return guarded([&]() -> anova_status {
+        if (P < 1 || P > kMaxWindows) return fail(ANOVA_ERR_INVALID_ARG, "P must be in [1, 64]");
+        std::vector<double> ell(P, sigma);
+        return create_plan(points, n, d, windows, P, ell.data(), nullptr, N, m, flags, cuda_stream, out);
+    });
+}
+
+anova_status anova_nfft_plan_ex(const double *points, int64_t n, int d, const int32_t *windows,
+                                int P, const double *ell, const double *eta, int N, int m,
+                                int flags, void *cuda_stream, anova_plan_t *out) {
+    return guarded([&]() -> anova_status {
+        return create_plan(points, n, d, windows, P, ell, eta, N, m, flags, cuda_stream, out);
+    });
+}
+
+anova_status anova_matvec(anova_plan_t plan, const void *v, void *Kv, int nrhs) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!v || !Kv) return fail(ANOVA_ERR_INVALID_ARG, "v or Kv is NULL");
+        if (nrhs < 1) return fail(ANOVA_ERR_INVALID_ARG, "nrhs must be >= 1");
+        const size_t bytes = elem_size(plan) * (size_t)plan->n * nrhs;
+        const char *a = (const char *)v, *b = (const char *)Kv;
+        if (a < b + bytes && b < a + bytes) return fail(ANOVA_ERR_INVALID_ARG, "v and Kv overlap");
+        DeviceGuard g(plan->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        if (plan->prec == ANOVA_FP64) return run_matvec_t<double>(plan, v, Kv, nrhs, -1);
+        return run_matvec_t<float>(plan, v, Kv, nrhs, -1);
+    });
+}
+
+anova_status anova_matvec_host(anova_plan_t plan, const void *v_host, void *Kv_host, int nrhs) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!v_host || !Kv_host) return fail(ANOVA_ERR_INVALID_ARG, "v or Kv is NULL");
+        if (nrhs < 1) return fail(ANOVA_ERR_INVALID_ARG, "nrhs must be >= 1");
+        DeviceGuard g(plan->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        const size_t bytes = elem_size(plan) * (size_t)plan->n * nrhs;
+        if (nrhs > plan->stage_rhs) {
+            cudaStreamSynchronize(plan->stream);
+            if (plan->dv) cudaFree(plan->dv);
+            if (plan->dkv) cudaFree(plan->dkv);
+            plan->dv = plan->dkv = nullptr;
+            plan->stage_rhs = 0;
+            cudaError_t e;
+            if ((e = cudaMalloc(&plan->dv, bytes)) != cudaSuccess ||
+                (e = cudaMalloc(&plan->dkv, bytes)) != cudaSuccess)
+                return fail(ANOVA_ERR_OOM, "staging allocation failed");
+            plan->stage_rhs = nrhs;
+        }
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(plan->dv, v_host, bytes, cudaMemcpyHostToDevice, plan->stream));
+        anova_status st = plan->prec == ANOVA_FP64
+                              ? run_matvec_t<double>(plan, plan->dv, plan->dkv, nrhs, -1)
+                              : run_matvec_t<float>(plan, plan->dv, plan->dkv, nrhs, -1);
+        if (st != ANOVA_OK) return st;
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(Kv_host, plan->dkv, bytes, cudaMemcpyDeviceToHost, plan->stream));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+        return ANOVA_OK;
+    });
+}
+
+static anova_status window_index(anova_plan_t plan, int l, int *w) {
+    if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+    if (l < 0 || l >= plan->P) return fail(ANOVA_ERR_INVALID_ARG, "window index out of range");
+    *w = plan->user_to_internal[l];
+    return ANOVA_OK;
+}
+
+anova_status anova_window_matvec(anova_plan_t plan, int l, const void *v, void *Kv) {
+    return guarded([&]() -> anova_status {
+        int w;
+        anova_status st = window_index(plan, l, &w);
+        if (st != ANOVA_OK) return st;
+        if (!v || !Kv) return fail(ANOVA_ERR_INVALID_ARG, "v or Kv is NULL");
+        DeviceGuard g(plan->device);
+        if (plan->prec == ANOVA_FP64) return run_matvec_t<double>(plan, v, Kv, 1, w);
+        return run_matvec_t<float>(plan, v, Kv, 1, w);
+    });
+}
+
+anova_status anova_spread_grid(anova_plan_t plan, int l, const void *v, void *grid) {
+    return guarded([&]() -> anova_status {
+        int w;
+        anova_status st = window_index(plan, l, &w);
+        if (st != ANOVA_OK) return st;
+        if (!v || !grid) return fail(ANOVA_ERR_INVALID_ARG, "NULL buffer");
+        DeviceGuard g(plan->device);
+        if (plan->prec == ANOVA_FP64) return run_spread_grid_t<double>(plan, w, v, grid);
+        return run_spread_grid_t<float>(plan, w, v, grid);
+    });
+}
+
+anova_status anova_conv_grid(anova_plan_t plan, int l, const void *grid_in, void *grid_out) {
+    return guarded([&]() -> anova_status {
+        int w;
+        anova_status st = window_index(plan, l, &w);
+        if (st != ANOVA_OK) return st;
+        if (!grid_in || !grid_out) return fail(ANOVA_ERR_INVALID_ARG, "NULL buffer");
+        DeviceGuard g(plan->device);
+        if (plan->prec == ANOVA_FP64) return run_conv_grid_t<double>(plan, w, grid_in, grid_out);
+        return run_conv_grid_t<float>(plan, w, grid_in, grid_out);
+    });
+}
+
+anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void *f) {
+    return guarded([&]() -> anova_status {
+        int w;
+        anova_status st = window_index(plan, l, &w);
+        if (st != ANOVA_OK) return st;
+        if (!grid || !f) return fail(ANOVA_ERR_INVALID_ARG, "NULL buffer");
+        DeviceGuard g(plan->device);
+        if (plan->prec == ANOVA_FP64) return run_interp_grid_t<double>(plan, w, grid, f);
+        return run_interp_grid_t<float>(plan, w, grid, f);
+    });
+}
+
+anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
+                             int64_t *device_bytes) {
+    if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+    if (n) *n = plan->n;
+    if (P) *P = plan->P;
+    if (n_os) *n_os = plan->n_os;
+    if (flags) *flags = plan->prec;
+    if (device_bytes) *device_bytes = plan->static_bytes + plan->ws_bytes;
+    return ANOVA_OK;
+}
+
+void anova_plan_destroy(anova_plan_t plan) {
+    if (!plan) return;
+    DeviceGuard g(plan->device);
+    cudaStreamSynchronize(plan->stream);
+    release_timing(plan);
+    destroy_plan(plan);
+}
+
+anova_status anova_plan_set_timing(anova_plan_t plan, int enable) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        DeviceGuard g(plan->device);
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+        reset_timing(plan);
+        plan->timing = enable != 0;
+        return ANOVA_OK;
+    });
+}
+
+anova_status anova_plan_stage_times(anova_plan_t plan, double *ms, int64_t *launches) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        DeviceGuard g(plan->device);
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+        double acc[NUM_STAGES] = {0, 0, 0, 0, 0};
+        for (auto &x : plan->evts) {
+            float t = 0.f;
+            ANOVA_CUDA_TRY(cudaEventElapsedTime(&t, x.a, x.b));
+            acc[x.stage] += t;
+        }
+        if (ms)
+            for (int s = 0; s < NUM_STAGES; ++s) ms[s] = acc[s];
+        if (launches) *launches = plan->launches;
+        return ANOVA_OK;
+    });
+}
+
+anova_status anova_kernel_coeffs(double ell, int N, double *b) {
+    return guarded([&]() -> anova_status {
+        if (!b) return fail(ANOVA_ERR_INVALID_ARG, "b is NULL");
+        if (N < 2 || N > 1024 || (N & 1)) return fail(ANOVA_ERR_INVALID_ARG, "N must be even, 2..1024");
+        if (!(ell > 0.0) || !std::isfinite(ell)) return fail(ANOVA_ERR_INVALID_ARG, "ell must be positive");
+        std::vector<double> c;
+        if (!kernel_coeffs(ell, N, c)) return fail(ANOVA_ERR_INVALID_ARG, "coefficient fit failed");
+        std::memcpy(b, c.data(), sizeof(double) * c.size());
+        return ANOVA_OK;
+    });
+}
+
+anova_status anova_window_hat(int m, int n_os, int count, double *Psi) {
+    return guarded([&]() -> anova_status {
+        if (!Psi || count < 0) return fail(ANOVA_ERR_INVALID_ARG, "bad output");
+        if (m < 1 || m > 16 || n_os < 2 * m) return fail(ANOVA_ERR_INVALID_ARG, "bad m / n_os");
+        window_hat(m, n_os, count, Psi);
+        return ANOVA_OK;
+    });
+}
+
+const char *anova_last_error(void) { return g_last_error.c_str(); }
+
+const char *anova_version(void) { return "anova-nfft-gb300 0.1"; }
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Device building blocks shared by the spread / interpolation / FFT kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "anova_internal.h"
+
+namespace anova {
+
+// Window polynomial coefficients (FP32 kernels) and Kaiser-Bessel constants (FP64 kernels),
+// passed by value so that they live in the kernel-parameter constant bank.
+struct WinParams {
+    float c[16][kPolyDeg + 1];  // c[j][p]: psi(f + m - 1 - j) ~ sum_p c z^p, z = 2f - 1
+    double beta;                // Kaiser-Bessel shape pi (2 - 1/oversampling)
+    double scale;               // m / sinh(beta m): normalises psi(0) to 1
+};
+
+// The 2M window weights of one coordinate with fractional cell offset f in [0, 1):
+// w[j] = psi(f + M - 1 - j), the weight of grid point c - M + 1 + j for a point in cell c.
+template <typename T, int M>
+struct Weights;
+
+template <int M>
+struct Weights<float, M> {
+    static __device__ __forceinline__ void eval(float f, const WinParams &wp, float *w) {
+        const float z = fmaf(2.0f, f, -1.0f);
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j) {
+            float acc = wp.c[j][kPolyDeg];
+#pragma unroll
+            for (int p = kPolyDeg - 1; p >= 0; --p) acc = fmaf(acc, z, wp.c[j][p]);
+            w[j] = acc;
+        }
+    }
+};
+
+template <int M>
+struct Weights<double, M> {
+    static __device__ __forceinline__ void eval(double f, const WinParams &wp, double *w) {
+#pragma unroll
+        for (int j = 0; j < 2 * M; ++j) {
+            const double t = f + (double)(M - 1 - j);
+            const double s2 = (double)(M * M) - t * t;
+            double val;
+            if (s2 <= 0.0) {
+                val = (s2 == 0.0) ? wp.beta * wp.scale : 0.0;
+            } else {
+                const double s = sqrt(s2);
+                if (s < 1e-4) {
+                    const double bs2 = wp.beta * wp.beta * s2;
+                    val = wp.beta * (1.0 + bs2 * (1.0 / 6.0) + bs2 * bs2 * (1.0 / 120.0)) * wp.scale;
+                } else {
+                    val = sinh(wp.beta * s) / s * wp.scale;
+                }
+            }
+            w[j] = val;
+        }
+    }
+};
+
+__device__ __forceinline__ int cell_coord(int packed, int k) { return (packed >> (10 * k)) & 1023; }
+
+// Load n contiguous T from 16-byte aligned shared memory.
+template <typename T, int CNT>
+__device__ __forceinline__ void lds_vec(const T *p, T *out) {
+    if constexpr (sizeof(T) == 4 && CNT % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < CNT / 4; ++i) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[i];
+            out[4 * i + 0] = q.x;
+            out[4 * i + 1] = q.y;
+            out[4 * i + 2] = q.z;
+            out[4 * i + 3] = q.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && CNT % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < CNT / 2; ++i) {
+            const double2 q = reinterpret_cast<const double2 *>(p)[i];
+            out[2 * i + 0] = q.x;
+            out[2 * i + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < CNT; ++i) out[i] = p[i];
+    }
+}
+
+template <int DW, int M>
+struct Geo {
+    static constexpr int W2 = 2 * M;                                   // footprint edge
+    static constexpr int ROWS = DW == 3 ? W2 * W2 : (DW == 2 ? W2 : 1); // rows of the last dim
+    static constexpr int RPL = (ROWS + 31) / 32;                       // rows per lane
+    static constexpr int WS = (W2 + 3) / 4 * 4;                        // padded weights per dim
+    static constexpr int PSTRIDE = DW * WS;                            // staged weights per point
+    static constexpr int VOL = DW == 3 ? W2 * W2 * W2 : (DW == 2 ? W2 * W2 : W2);
+};
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+}  // namespace anova

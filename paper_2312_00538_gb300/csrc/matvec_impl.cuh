@@ -1,0 +1,347 @@
+// Host-side launch sequence of one fast-summation matvec (spread -> reduce -> per-axis
+// FFT/scale/IFFT -> interpolation -> window sum), templated on the element type.
+#pragma once
+
+#include <algorithm>
+
+#include "conv_kernels.cuh"
+#include "nfft_kernels.cuh"
+
+namespace anova {
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static constexpr int B = 4;
+    static constexpr int SPREAD_WARPS = 8;
+    static constexpr int INTERP_WARPS = 8;
+};
+template <>
+struct Prec<double> {
+    static constexpr int B = 2;
+    static constexpr int SPREAD_WARPS = 4;
+    static constexpr int INTERP_WARPS = 4;
+};
+
+template <typename T, int DW, int M>
+cudaError_t launch_spread_t(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
+    constexpr int B = Prec<T>::B, NW = Prec<T>::SPREAD_WARPS;
+    using C = SpreadCfg<T, DW, M, B, NW>;
+    auto kern = k_spread<T, DW, M, B, NW>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int DW, int M>
+cudaError_t launch_interp_t(const InterpArgs &a, int nseg, int nrhs, cudaStream_t st) {
+    constexpr int NW = Prec<T>::INTERP_WARPS;
+    using C = InterpCfg<T, DW, M, NW>;
+    auto kern = k_interp<T, DW, M, NW>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<dim3((nseg + NW - 1) / NW, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NOS, int DW>
+cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t st) {
+    using C = ConvCfg<T, NOS>;
+    auto kern = k_conv<T, NOS, DW>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<dim3(ntiles, nrhs), 256, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// runtime (dw, m) -> template dispatch
+template <typename T, int DW>
+cudaError_t dispatch_spread_m(int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        switch (m) {
+            case 2: return launch_spread_t<T, DW, 2>(a, nb, nrhs, st);
+            case 3: return launch_spread_t<T, DW, 3>(a, nb, nrhs, st);
+            case 4: return launch_spread_t<T, DW, 4>(a, nb, nrhs, st);
+            case 5: return launch_spread_t<T, DW, 5>(a, nb, nrhs, st);
+            case 6: return launch_spread_t<T, DW, 6>(a, nb, nrhs, st);
+        }
+    } else {
+        switch (m) {
+            case 3: return launch_spread_t<T, DW, 3>(a, nb, nrhs, st);
+            case 4: return launch_spread_t<T, DW, 4>(a, nb, nrhs, st);
+            case 5: return launch_spread_t<T, DW, 5>(a, nb, nrhs, st);
+            case 6: return launch_spread_t<T, DW, 6>(a, nb, nrhs, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t dispatch_spread(int dw, int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
+    switch (dw) {
+        case 1: return dispatch_spread_m<T, 1>(m, a, nb, nrhs, st);
+        case 2: return dispatch_spread_m<T, 2>(m, a, nb, nrhs, st);
+        case 3: return dispatch_spread_m<T, 3>(m, a, nb, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int DW>
+cudaError_t dispatch_interp_m(int m, const InterpArgs &a, int nseg, int nrhs, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        switch (m) {
+            case 2: return launch_interp_t<T, DW, 2>(a, nseg, nrhs, st);
+            case 3: return launch_interp_t<T, DW, 3>(a, nseg, nrhs, st);
+            case 4: return launch_interp_t<T, DW, 4>(a, nseg, nrhs, st);
+            case 5: return launch_interp_t<T, DW, 5>(a, nseg, nrhs, st);
+            case 6: return launch_interp_t<T, DW, 6>(a, nseg, nrhs, st);
+        }
+    } else {
+        switch (m) {
+            case 3: return launch_interp_t<T, DW, 3>(a, nseg, nrhs, st);
+            case 4: return launch_interp_t<T, DW, 4>(a, nseg, nrhs, st);
+            case 5: return launch_interp_t<T, DW, 5>(a, nseg, nrhs, st);
+            case 6: return launch_interp_t<T, DW, 6>(a, nseg, nrhs, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t dispatch_interp(int dw, int m, const InterpArgs &a, int nseg, int nrhs,
+                            cudaStream_t st) {
+    switch (dw) {
+        case 1: return dispatch_interp_m<T, 1>(m, a, nseg, nrhs, st);
+        case 2: return dispatch_interp_m<T, 2>(m, a, nseg, nrhs, st);
+        case 3: return dispatch_interp_m<T, 3>(m, a, nseg, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int NOS>
+cudaError_t dispatch_conv_dw(int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
+    switch (dw) {
+        case 1: return launch_conv_t<T, NOS, 1>(a, nt, nrhs, st);
+        case 2: return launch_conv_t<T, NOS, 2>(a, nt, nrhs, st);
+        case 3: return launch_conv_t<T, NOS, 3>(a, nt, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t dispatch_conv(int n_os, int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
+    switch (n_os) {
+        case 32: return dispatch_conv_dw<T, 32>(dw, a, nt, nrhs, st);
+        case 64: return dispatch_conv_dw<T, 64>(dw, a, nt, nrhs, st);
+        case 128: return dispatch_conv_dw<T, 128>(dw, a, nt, nrhs, st);
+        case 256: return dispatch_conv_dw<T, 256>(dw, a, nt, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+WinParams make_winparams(const anova_plan *p) {
+    WinParams wp{};
+    for (int j = 0; j < 2 * p->m && j < 16; ++j)
+        for (int q = 0; q <= kPolyDeg; ++q) wp.c[j][q] = (float)p->poly[(size_t)j * (kPolyDeg + 1) + q];
+    wp.beta = kb_beta();
+    wp.scale = p->m / std::sinh(wp.beta * p->m);
+    return wp;
+}
+
+template <typename T>
+int tile_volume(const anova_plan *p, int dw) {
+    const int tw = Prec<T>::B + 2 * p->m - 1;
+    int tv = 1;
+    for (int k = 0; k < dw; ++k) tv *= tw;
+    return tv;
+}
+
+// Partial tiles of windows [a0, a1) onto grid0: per-bin sums of multi-item bins, then the
+// gather of bin tiles onto every grid point of the windows' boxes.
+template <typename T>
+anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, long long grid_stride,
+                           int nrhs, int zero_offset) {
+    cudaStream_t st = p->stream;
+    BinReduceArgs ba;
+    ba.tiles = p->tiles;
+    ba.mbins = p->mbins;
+    ba.mb_begin = p->win[a0].mb_begin;
+    ba.nmbins = p->win[a1 - 1].mb_end - ba.mb_begin;
+    ba.nrhs = nrhs;
+    if (ba.nmbins > 0) {
+        k_bin_reduce<T><<<dim3(ba.nmbins, nrhs), 256, 0, st>>>(ba);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+    }
+    ReduceArgs ra;
+    ra.tiles = p->tiles;
+    ra.grid0 = grid0;
+    ra.dwin = p->dwin;
+    ra.bins = p->bins;
+    ra.grid_total = grid_stride;
+    ra.w_begin = a0;
+    ra.w_end = a1;
+    ra.nrhs = nrhs;
+    ra.n_os = p->n_os;
+    ra.NB = p->NB;
+    ra.M = p->m;
+    ra.B = Prec<T>::B;
+    ra.zero_offset = zero_offset;
+    ra.box_cum[0] = 0;
+    for (int w = a0; w < a1; ++w) ra.box_cum[w - a0 + 1] = ra.box_cum[w - a0] + p->win[w].box_volume();
+    const long long vol = ra.box_cum[a1 - a0];
+    if (vol > 0) {
+        const int nb = (int)((vol + 255) / 256);
+        if (dw == 3) k_reduce<T, 3><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
+        else if (dw == 2) k_reduce<T, 2><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
+        else k_reduce<T, 1><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+    }
+    return ANOVA_OK;
+}
+
+// One matvec over the window range [w0, w1) (all groups intersecting it). `part` receives
+// per-window results in original point order; grids g[0..3] are the workspace buffers.
+template <typename T>
+anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1, T *part,
+                            T *const g[4], long long grid_stride) {
+    cudaStream_t st = p->stream;
+    const WinParams wp = make_winparams<T>(p);
+    for (const Group &gr : p->groups) {
+        const int a0 = std::max(gr.w_begin, w0), a1 = std::min(gr.w_end, w1);
+        if (a0 >= a1) continue;
+        const int wi0 = p->win[a0].wi_begin, wi1 = p->win[a1 - 1].wi_end;
+        const int s0 = p->win[a0].seg_begin, s1 = p->win[a1 - 1].seg_end;
+        // 1. spread into partial tiles
+        SpreadArgs sa;
+        sa.wis = p->wis;
+        sa.segs = p->segs;
+        sa.frac = p->frac;
+        sa.perm = p->perm;
+        sa.v = v;
+        sa.tiles = p->tiles;
+        sa.n = p->n;
+        sa.total = p->n * p->P;
+        sa.nrhs = nrhs;
+        sa.wi_begin = wi0;
+        sa.wi_end = wi1;
+        sa.wp = wp;
+        cudaEvent_t e0 = stage_event(p);
+        if (wi1 > wi0) {
+            cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nrhs, st);
+            if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+            p->launches += 1;
+        }
+        cudaEvent_t e1 = stage_event(p);
+        stage_record(p, STAGE_SPREAD, e0, e1);
+        // 2. reduce partial tiles onto the grid boxes
+        {
+            anova_status rs = launch_reduce<T>(p, gr.dw, a0, a1, g[0], grid_stride, nrhs, 0);
+            if (rs != ANOVA_OK) return rs;
+        }
+        cudaEvent_t e2 = stage_event(p);
+        stage_record(p, STAGE_REDUCE, e1, e2);
+        // 3. axis passes: g0 -> g1 -> g2 -> g3 (the last pass always writes g3)
+        for (int pass = 0; pass < gr.dw; ++pass) {
+            ConvArgs ca;
+            ca.tiles = p->ftiles;
+            ca.in = pass == 0 ? g[0] : g[pass];
+            ca.out = pass == gr.dw - 1 ? g[3] : g[pass + 1];
+            ca.D1br = p->D1br;
+            ca.tw = p->tw;
+            ca.dwin = p->dwin;
+            ca.grid_stride_rhs = grid_stride;
+            ca.tile_begin = p->win[a0].tile_begin[pass];
+            ca.tile_end = p->win[a1 - 1].tile_end[pass];
+            ca.zero_offset = 0;
+            const int nt = ca.tile_end - ca.tile_begin;
+            if (nt > 0) {
+                cudaError_t e = dispatch_conv<T>(p->n_os, gr.dw, ca, nt, nrhs, st);
+                if (e != cudaSuccess) return cuda_fail(e, "conv launch");
+                p->launches += 1;
+            }
+        }
+        cudaEvent_t e3 = stage_event(p);
+        stage_record(p, STAGE_FFT, e2, e3);
+        // 4. interpolation
+        InterpArgs ia;
+        ia.segs = p->segs;
+        ia.frac = p->frac;
+        ia.perm = p->perm;
+        ia.grid = g[3];
+        ia.dwin = p->dwin;
+        ia.part = part;
+        ia.n = p->n;
+        ia.total = p->n * p->P;
+        ia.grid_stride_rhs = grid_stride;
+        ia.nrhs = nrhs;
+        ia.seg_begin = s0;
+        ia.seg_end = s1;
+        ia.n_os = p->n_os;
+        ia.zero_offset = 0;
+        ia.part_w0 = w0;
+        ia.wp = wp;
+        if (s1 > s0) {
+            cudaError_t e = dispatch_interp<T>(gr.dw, p->m, ia, s1 - s0, nrhs, st);
+            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+            p->launches += 1;
+        }
+        cudaEvent_t e4 = stage_event(p);
+        stage_record(p, STAGE_INTERP, e3, e4);
+    }
+    return ANOVA_OK;
+}
+
+template <typename T>
+anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_window) {
+    const int chunk = std::min(nrhs, 16);
+    anova_status st = ensure_workspace(p, chunk);
+    if (st != ANOVA_OK) return st;
+    T *grids = reinterpret_cast<T *>(p->grids);
+    const long long gs = p->grid_total;
+    T *g[4];
+    for (int k = 0; k < 4; ++k) g[k] = grids + (size_t)k * p->ws_rhs * gs;
+    T *part = reinterpret_cast<T *>(p->part);
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+        const int nr = std::min(chunk, nrhs - r0);
+        const T *vr = v + (size_t)r0 * p->n;
+        T *kr = Kv + (size_t)r0 * p->n;
+        if (only_window >= 0) {
+            // the single window's result goes straight to Kv (part_w0 = only_window)
+            st = matvec_windows<T>(p, vr, nr, only_window, only_window + 1, kr, g, gs);
+            if (st != ANOVA_OK) return st;
+        } else {
+            st = matvec_windows<T>(p, vr, nr, 0, p->P, part, g, gs);
+            if (st != ANOVA_OK) return st;
+            const long long tot = p->n * nr;
+            const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
+            cudaEvent_t e0 = stage_event(p);
+            k_window_sum<T><<<nb, 256, 0, p->stream>>>(part, kr, p->n, nr, p->P);
+            ANOVA_CUDA_TRY(cudaGetLastError());
+            p->launches += 1;
+            stage_record(p, STAGE_SUM, e0, stage_event(p));
+        }
+    }
+    return ANOVA_OK;
+}
+
+}  // namespace anova

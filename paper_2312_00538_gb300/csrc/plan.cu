@@ -1,0 +1,620 @@
+// Plan construction of the ANOVA-NFFT fast summation (arXiv 2312.00538, Sec. 3): per window,
+// points are binned by the oversampled-grid cell that holds them and sorted (stable LSD radix
+// sort on the device), fractional cell offsets are stored in sorted order, and the host derives
+// the cell segments, spread work items, bin tables, grid boxes and FFT line tiles from the
+// sorted keys. The host also computes the FP64 plan constants (Fourier coefficients of the
+// kernel, window transform, window polynomials, twiddles).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "anova_internal.h"
+
+namespace anova {
+
+namespace {
+
+constexpr int kSortTile = 4096;
+
+__global__ void k_keys(const double *__restrict__ X, long long n, int d, const int *__restrict__ feat,
+                       const int *__restrict__ dws, int P, int n_os, int B, int NB, int KB,
+                       uint32_t *__restrict__ keys, int *__restrict__ vals) {
+    const long long total = n * P;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(q / n);
+        const long long i = q - (long long)w * n;
+        const int dw = dws[w];
+        uint32_t bin = 0, loc = 0;
+        for (int k = 0; k < dw; ++k) {
+            const double s = (X[i * d + feat[3 * w + k]] + 0.5) * n_os;
+            int c = (int)floor(s);
+            c = min(max(c, 0), n_os - 1);
+            bin = bin * NB + (uint32_t)(c / B);
+            loc = loc * B + (uint32_t)(c % B);
+        }
+        uint32_t bvol = 1;
+        for (int k = 0; k < dw; ++k) bvol *= (uint32_t)B;
+        keys[q] = ((uint32_t)w << KB) | (bin * bvol + loc);
+        vals[q] = (int)i;
+    }
+}
+
+__global__ void k_radix_hist(const uint32_t *__restrict__ keys, long long cnt, int shift,
+                             int *__restrict__ hist, int nblk) {
+    __shared__ int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const long long b0 = (long long)blockIdx.x * kSortTile;
+    const long long b1 = min(cnt, b0 + kSortTile);
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+        atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * nblk + blockIdx.x] = h[i];
+}
+
+// exclusive scan of len ints in place, one block of 1024 threads
+__global__ void k_scan_exclusive(int *data, long long len) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x;
+    const long long per = (len + 1023) / 1024;
+    const long long a = t * per, b = min(len, a + per);
+    long long s = 0;
+    for (long long i = a; i < b; ++i) s += data[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = t == 0 ? 0 : part[t - 1];
+    for (long long i = a; i < b; ++i) {
+        const int x = data[i];
+        data[i] = (int)run;
+        run += x;
+    }
+}
+
+// stable scatter: one warp per tile, items taken in order 32 at a time
+__global__ void k_radix_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+                                uint32_t *__restrict__ kout, int *__restrict__ vout, long long cnt,
+                                int shift, const int *__restrict__ offs, int nblk) {
+    __shared__ int base[256];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < 256; i += 32) base[i] = offs[(long long)i * nblk + blockIdx.x];
+    __syncwarp();
+    const long long b0 = (long long)blockIdx.x * kSortTile;
+    const long long b1 = min(cnt, b0 + kSortTile);
+    const unsigned lt = (1u << lane) - 1u;
+    for (long long c = b0; c < b1; c += 32) {
+        const long long i = c + lane;
+        const bool valid = i < b1;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const int dig = valid ? (int)((key >> shift) & 255u) : 256 + lane;
+        const unsigned mask = __match_any_sync(0xffffffffu, dig);
+        const int rank = __popc(mask & lt);
+        int pos = 0;
+        if (valid) pos = base[dig] + rank;
+        __syncwarp();
+        if (valid) {
+            kout[pos] = key;
+            vout[pos] = vin[i];
+            if ((mask & lt) == 0) base[dig] += __popc(mask);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void k_gather(const uint32_t *__restrict__ keys, const int *__restrict__ vals,
+                         const double *__restrict__ X, long long n, int d,
+                         const int *__restrict__ feat, const int *__restrict__ dws, int P, int n_os,
+                         int KB, T *__restrict__ frac, int *__restrict__ perm) {
+    const long long total = n * P;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(keys[q] >> KB);
+        const int i = vals[q];
+        const int dw = dws[w];
+        for (int k = 0; k < 3; ++k) {
+            T f = T(0);
+            if (k < dw) {
+                const double s = (X[(long long)i * d + feat[3 * w + k]] + 0.5) * n_os;
+                double c = floor(s);
+                c = fmin(fmax(c, 0.0), (double)(n_os - 1));
+                f = (T)(s - c);
+            }
+            frac[(long long)k * total + q] = f;
+        }
+        perm[q] = i;
+    }
+}
+
+int ilog2(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
+int bitrev(int x, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+template <typename T>
+void free_dev(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+size_t elem_size(const anova_plan *p) { return p->prec == ANOVA_FP64 ? sizeof(double) : sizeof(float); }
+
+void release_workspace(anova_plan *p) {
+    if (p->grids) cudaFree(p->grids);
+    if (p->tiles) cudaFree(p->tiles);
+    if (p->part) cudaFree(p->part);
+    p->grids = p->tiles = p->part = nullptr;
+    p->ws_rhs = 0;
+    p->ws_bytes = 0;
+}
+
+anova_status ensure_workspace(anova_plan *p, int nrhs) {
+    if (nrhs <= p->ws_rhs) return ANOVA_OK;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    release_workspace(p);
+    const size_t es = elem_size(p);
+    const int B = p->B;
+    const int tw = B + 2 * p->m - 1;
+    const size_t tv = (size_t)tw * tw * tw;
+    const size_t gbytes = es * 4 * (size_t)nrhs * p->grid_total;
+    const size_t tbytes = es * std::max<size_t>(1, (size_t)p->nwi * nrhs * tv);
+    const size_t pbytes = es * (size_t)p->P * nrhs * p->n;
+    if ((e = cudaMalloc(&p->grids, gbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&p->tiles, tbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&p->part, pbytes)) != cudaSuccess) {
+        release_workspace(p);
+        return fail(ANOVA_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(p->grids, 0, gbytes, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    p->ws_rhs = nrhs;
+    p->ws_bytes = (int64_t)(gbytes + tbytes + pbytes);
+    return ANOVA_OK;
+}
+
+void destroy_plan(anova_plan *p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    release_workspace(p);
+    void *bufs[] = {p->frac, p->perm, p->segs, p->wis, p->bins, p->mbins, p->ftiles, p->dwin,
+                    p->D1br, p->tw, p->dv, p->dkv};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                         const double *ell, const double *eta, int N, int m, int flags,
+                         void *stream, anova_plan_t *out) {
+    // ------------------------------------------------------------------ validation
+    if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!points || !windows || !ell) return fail(ANOVA_ERR_INVALID_ARG, "NULL input pointer");
+    if (n < 1 || n > (int64_t)1 << 30) return fail(ANOVA_ERR_INVALID_ARG, "n must be in [1, 2^30]");
+    if (d < 1) return fail(ANOVA_ERR_INVALID_ARG, "d must be >= 1");
+    if (P < 1 || P > kMaxWindows) return fail(ANOVA_ERR_INVALID_ARG, "P must be in [1, 64]");
+    if ((int64_t)n * P > ((int64_t)1 << 31) - 1) return fail(ANOVA_ERR_INVALID_ARG, "n * P exceeds 2^31 - 1");
+    const int prec = flags & 1;
+    if (flags & ~1) return fail(ANOVA_ERR_INVALID_ARG, "unknown flag bits");
+    if (N != 16 && N != 32 && N != 64 && N != 128)
+        return fail(ANOVA_ERR_INVALID_ARG, "N must be an even power of two in {16, 32, 64, 128}");
+    if (prec == ANOVA_FP32 ? (m < 2 || m > 6) : (m < 3 || m > 6))
+        return fail(ANOVA_ERR_INVALID_ARG, "m out of range (FP32: 2..6, FP64: 3..6)");
+    for (int l = 0; l < P; ++l) {
+        if (!(ell[l] > 0.0) || !std::isfinite(ell[l]))
+            return fail(ANOVA_ERR_INVALID_ARG, "kernel length scale must be positive and finite");
+        if (eta && !std::isfinite(eta[l])) return fail(ANOVA_ERR_NONFINITE, "window weight not finite");
+        int cnt = 0;
+        bool ended = false;
+        for (int k = 0; k < 3; ++k) {
+            const int f = windows[3 * l + k];
+            if (f < 0) {
+                if (f != -1) return fail(ANOVA_ERR_INVALID_ARG, "window padding must be -1");
+                ended = true;
+                continue;
+            }
+            if (ended) return fail(ANOVA_ERR_INVALID_ARG, "window padding must follow valid entries");
+            if (f >= d) return fail(ANOVA_ERR_INVALID_ARG, "window feature index >= d");
+            for (int k2 = 0; k2 < k; ++k2)
+                if (windows[3 * l + k2] == f) return fail(ANOVA_ERR_INVALID_ARG, "repeated feature in a window");
+            ++cnt;
+        }
+        if (cnt == 0) return fail(ANOVA_ERR_INVALID_ARG, "empty window");
+    }
+    {
+        std::vector<char> used(d, 0);
+        for (int l = 0; l < P; ++l)
+            for (int k = 0; k < 3; ++k)
+                if (windows[3 * l + k] >= 0) used[windows[3 * l + k]] = 1;
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < d; ++k) {
+                const double x = points[i * d + k];
+                if (!std::isfinite(x)) return fail(ANOVA_ERR_NONFINITE, "points hold NaN or Inf");
+                if (used[k] && (x < -kBoxHalf - 1e-12 || x > kBoxHalf + 1e-12))
+                    return fail(ANOVA_ERR_OUT_OF_RANGE, "a point coordinate lies outside [-0.2, 0.2]");
+            }
+    }
+    std::unique_ptr<anova_plan, void (*)(anova_plan *)> plan(new (std::nothrow) anova_plan(),
+                                                            destroy_plan);
+    if (!plan) return fail(ANOVA_ERR_OOM, "host allocation failed");
+    anova_plan *p = plan.get();
+    p->n = n;
+    p->d = d;
+    p->P = P;
+    p->N = N;
+    p->m = m;
+    p->n_os = 2 * N;
+    p->prec = prec;
+    p->B = prec == ANOVA_FP64 ? 2 : 4;
+    p->NB = p->n_os / p->B;
+    p->tile_w = p->B + 2 * m - 1;
+    p->stream = reinterpret_cast<cudaStream_t>(stream);
+    ANOVA_CUDA_TRY(cudaGetDevice(&p->device));
+    const int nos = p->n_os;
+    const size_t es = elem_size(p);
+
+    // ------------------------------------------------------------------ windows (grouped by dw)
+    std::vector<int> order(P);
+    for (int l = 0; l < P; ++l) order[l] = l;
+    auto dw_of = [&](int l) {
+        int c = 0;
+        for (int k = 0; k < 3; ++k) c += windows[3 * l + k] >= 0;
+        return c;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dw_of(a) > dw_of(b); });
+    p->win.resize(P);
+    p->user_to_internal.assign(P, 0);
+    for (int w = 0; w < P; ++w) {
+        const int l = order[w];
+        p->user_to_internal[l] = w;
+        WindowInfo &wi = p->win[w];
+        wi.dw = dw_of(l);
+        for (int k = 0; k < 3; ++k) wi.feat[k] = windows[3 * l + k];
+        wi.ell = ell[l];
+        wi.eta = eta ? eta[l] : 1.0;
+    }
+
+    // ------------------------------------------------------------------ host constants
+    if (!window_poly(m, kPolyDeg, p->poly)) return fail(ANOVA_ERR_INVALID_ARG, "window polynomial fit failed");
+    const int lb = ilog2(nos);
+    // deconvolution diagonal per window and axis, bit-reversed; eta_l scales the axis-0 copy
+    std::vector<double> d1br((size_t)P * 3 * nos, 0.0);
+    for (int w = 0; w < P; ++w) {
+        std::vector<double> D1;
+        if (!deconv_diag(p->win[w].ell, N, m, nos, D1))
+            return fail(ANOVA_ERR_INVALID_ARG, "kernel coefficient fit failed");
+        for (int ax = 0; ax < 3; ++ax)
+            for (int e = 0; e < nos; ++e)
+                d1br[((size_t)w * 3 + ax) * nos + e] = D1[bitrev(e, lb)] * (ax == 0 ? p->win[w].eta : 1.0);
+    }
+    std::vector<double> twid(nos);
+    for (int k = 0; k < nos / 2; ++k) {
+        twid[2 * k] = std::cos(-2.0 * M_PI * k / nos);
+        twid[2 * k + 1] = std::sin(-2.0 * M_PI * k / nos);
+    }
+
+    // ------------------------------------------------------------------ device sort
+    const long long total = (long long)n * P;
+    DevBuf dX, dfeat, ddws, dk0, dv0, dk1, dv1, dhist;
+    ANOVA_CUDA_TRY(cudaMalloc(&dX.p, sizeof(double) * n * d));
+    ANOVA_CUDA_TRY(cudaMalloc(&dfeat.p, sizeof(int) * 3 * P));
+    ANOVA_CUDA_TRY(cudaMalloc(&ddws.p, sizeof(int) * P));
+    ANOVA_CUDA_TRY(cudaMalloc(&dk0.p, sizeof(uint32_t) * total));
+    ANOVA_CUDA_TRY(cudaMalloc(&dv0.p, sizeof(int) * total));
+    ANOVA_CUDA_TRY(cudaMalloc(&dk1.p, sizeof(uint32_t) * total));
+    ANOVA_CUDA_TRY(cudaMalloc(&dv1.p, sizeof(int) * total));
+    std::vector<int> hfeat(3 * P), hdws(P);
+    for (int w = 0; w < P; ++w) {
+        hdws[w] = p->win[w].dw;
+        for (int k = 0; k < 3; ++k) hfeat[3 * w + k] = p->win[w].feat[k] < 0 ? 0 : p->win[w].feat[k];
+    }
+    cudaStream_t st = p->stream;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(dX.p, points, sizeof(double) * n * d, cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(dfeat.p, hfeat.data(), sizeof(int) * 3 * P, cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(ddws.p, hdws.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+    const int KB = 3 * lb;  // bits of the in-window key (enough for d_W <= 3)
+    const int keybits = KB + ilog2(P);
+    {
+        const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+        k_keys<<<nb, 256, 0, st>>>((const double *)dX.p, n, d, (const int *)dfeat.p, (const int *)ddws.p,
+                                   P, nos, p->B, p->NB, KB, (uint32_t *)dk0.p, (int *)dv0.p);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+    }
+    const int nblk = (int)((total + kSortTile - 1) / kSortTile);
+    ANOVA_CUDA_TRY(cudaMalloc(&dhist.p, sizeof(int) * 256 * (size_t)nblk));
+    uint32_t *kin = (uint32_t *)dk0.p, *kout = (uint32_t *)dk1.p;
+    int *vin = (int *)dv0.p, *vout = (int *)dv1.p;
+    for (int shift = 0; shift < keybits; shift += 8) {
+        k_radix_hist<<<nblk, 256, 0, st>>>(kin, total, shift, (int *)dhist.p, nblk);
+        k_scan_exclusive<<<1, 1024, 0, st>>>((int *)dhist.p, 256LL * nblk);
+        k_radix_scatter<<<nblk, 32, 0, st>>>(kin, vin, kout, vout, total, shift, (const int *)dhist.p, nblk);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    // sorted keys/values now in kin/vin
+    ANOVA_CUDA_TRY(cudaMalloc(&p->frac, es * 3 * total));
+    ANOVA_CUDA_TRY(cudaMalloc(&p->perm, sizeof(int) * total));
+    {
+        const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+        if (prec == ANOVA_FP64)
+            k_gather<double><<<nb, 256, 0, st>>>(kin, vin, (const double *)dX.p, n, d, (const int *)dfeat.p,
+                                                 (const int *)ddws.p, P, nos, KB, (double *)p->frac, p->perm);
+        else
+            k_gather<float><<<nb, 256, 0, st>>>(kin, vin, (const double *)dX.p, n, d, (const int *)dfeat.p,
+                                                (const int *)ddws.p, P, nos, KB, (float *)p->frac, p->perm);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<uint32_t> hkeys(total);
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(hkeys.data(), kin, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // ------------------------------------------------------------------ host tables
+    const int B = p->B, NB = p->NB;
+    const uint32_t kmask = (KB >= 32) ? 0xffffffffu : ((1u << KB) - 1u);
+    std::vector<int4> segs, wis, ftiles;
+    std::vector<int2> bins;
+    int64_t goff = 0;
+    // groups of consecutive windows with equal dw
+    for (int w = 0; w < P; ++w) {
+        if (p->groups.empty() || p->groups.back().dw != p->win[w].dw) {
+            Group g;
+            g.dw = p->win[w].dw;
+            g.w_begin = w;
+            p->groups.push_back(g);
+        }
+        p->groups.back().w_end = w + 1;
+    }
+    for (int w = 0; w < P; ++w) {
+        WindowInfo &wi = p->win[w];
+        const int dw = wi.dw;
+        int bvol = 1, nbins = 1;
+        for (int k = 0; k < dw; ++k) { bvol *= B; nbins *= NB; }
+        wi.seg_begin = (int)segs.size();
+        wi.wi_begin = (int)wis.size();
+        wi.bin_off = (int)bins.size();
+        bins.resize(bins.size() + nbins, make_int2(0, 0));
+        int cmin[3] = {nos, nos, nos}, cmax[3] = {-1, -1, -1};
+        const long long q0 = (long long)w * n, q1 = q0 + n;
+        uint32_t prev = 0xffffffffu;
+        int cur_bin = -1, wi_pts = 0;
+        for (long long q = q0; q < q1; ++q) {
+            const uint32_t key = hkeys[q] & kmask;
+            const bool new_cell = key != prev;
+            if (new_cell || segs.back().z >= kSegMax) {
+                const uint32_t bin = key / bvol, loc = key % bvol;
+                int c[3] = {0, 0, 0};
+                uint32_t bb = bin, ll = loc;
+                for (int k = dw - 1; k >= 0; --k) {
+                    c[k] = (int)(bb % NB) * B + (int)(ll % B);
+                    bb /= NB;
+                    ll /= B;
+                }
+                for (int k = 0; k < dw; ++k) {
+                    cmin[k] = std::min(cmin[k], c[k]);
+                    cmax[k] = std::max(cmax[k], c[k]);
+                }
+                const int packed = c[0] | (c[1] << 10) | (c[2] << 20);
+                segs.push_back(make_int4(packed, (int)q, 0, w));
+                // work items: runs of one bin's segments, at most kWiMax points
+                if ((int)bin != cur_bin || wi_pts + kSegMax > kWiMax) {
+                    int bc[3] = {0, 0, 0};
+                    uint32_t b2 = bin;
+                    for (int k = dw - 1; k >= 0; --k) { bc[k] = (int)(b2 % NB); b2 /= NB; }
+                    wis.push_back(make_int4(w, (int)segs.size() - 1, (int)segs.size(),
+                                            bc[0] | (bc[1] << 10) | (bc[2] << 20)));
+                    if ((int)bin != cur_bin) {
+                        bins[wi.bin_off + bin] = make_int2((int)wis.size() - 1, 0);
+                        cur_bin = (int)bin;
+                    }
+                    bins[wi.bin_off + bin].y += 1;
+                    wi_pts = 0;
+                    // tile of this bin must stay inside the grid
+                    for (int k = 0; k < dw; ++k) {
+                        const int lo = bc[k] * B - m + 1, hi = bc[k] * B + B + m - 1;
+                        if (lo < 0 || hi >= nos)
+                            return fail(ANOVA_ERR_INVALID_ARG, "bandwidth N too small for this window cut-off m");
+                    }
+                }
+                wis.back().z = (int)segs.size();
+                prev = key;
+            }
+            segs.back().z += 1;
+            wi_pts += 1;
+        }
+        wi.seg_end = (int)segs.size();
+        wi.wi_end = (int)wis.size();
+        for (int k = 0; k < dw; ++k) {
+            wi.box_lo[k] = cmin[k] - m + 1;
+            wi.box_hi[k] = cmax[k] + m + 1;
+        }
+        wi.grid_off = goff;
+        int64_t gsz = 1;
+        for (int k = 0; k < dw; ++k) gsz *= nos;
+        goff += gsz;
+    }
+    p->grid_total = goff;
+    // FFT tiles: group -> pass -> window
+    for (Group &g : p->groups) {
+        for (int pass = 0; pass < g.dw; ++pass) {
+            for (int w = g.w_begin; w < g.w_end; ++w) {
+                WindowInfo &wi = p->win[w];
+                wi.tile_begin[pass] = (int)ftiles.size();
+                int plo = 0, phi = 1, qlo = 0, qhi = 1;
+                if (g.dw == 3) {
+                    if (pass == 0) { plo = wi.box_lo[1]; phi = wi.box_hi[1]; qlo = wi.box_lo[2]; qhi = wi.box_hi[2]; }
+                    if (pass == 1) { plo = 0; phi = nos; qlo = wi.box_lo[2]; qhi = wi.box_hi[2]; }
+                    if (pass == 2) { plo = wi.box_lo[0]; phi = wi.box_hi[0]; qlo = wi.box_lo[1]; qhi = wi.box_hi[1]; }
+                } else if (g.dw == 2) {
+                    if (pass == 0) { qlo = wi.box_lo[1]; qhi = wi.box_hi[1]; }
+                    if (pass == 1) { qlo = wi.box_lo[0]; qhi = wi.box_hi[0]; }
+                }
+                for (int pp = plo; pp < phi; ++pp)
+                    for (int q = (qlo / 32) * 32; q < qhi; q += 32) ftiles.push_back(make_int4(w, pp, q, pass));
+                wi.tile_end[pass] = (int)ftiles.size();
+            }
+        }
+    }
+    // bins holding several work items (their partial tiles are summed before the grid gather)
+    std::vector<int4> mbins;
+    for (int w = 0; w < P; ++w) {
+        WindowInfo &wi = p->win[w];
+        int nbins = 1, tv = 1;
+        for (int k = 0; k < wi.dw; ++k) { nbins *= NB; tv *= (B + 2 * m - 1); }
+        wi.mb_begin = (int)mbins.size();
+        for (int b = 0; b < nbins; ++b) {
+            const int2 be = bins[wi.bin_off + b];
+            if (be.y > 1) mbins.push_back(make_int4(be.x, be.y, tv, 0));
+        }
+        wi.mb_end = (int)mbins.size();
+    }
+    p->nmbins = (int)mbins.size();
+    p->nseg = (int)segs.size();
+    p->nwi = (int)wis.size();
+    p->ntiles = (int)ftiles.size();
+
+    // ------------------------------------------------------------------ table invariants
+    // Every kernel index is derived from these tables; check them once here so that a table
+    // that would send a kernel outside its buffers is reported instead of launched.
+    {
+        std::vector<int> hperm(total);
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(hperm.data(), p->perm, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<char> seen(n);
+        for (int w = 0; w < P; ++w) {
+            std::fill(seen.begin(), seen.end(), 0);
+            for (long long q = (long long)w * n; q < (long long)(w + 1) * n; ++q) {
+                const int i = hperm[q];
+                if (i < 0 || i >= n || seen[i]) return fail(ANOVA_ERR_CUDA, "plan check: sort did not produce a permutation");
+                seen[i] = 1;
+                if (q > (long long)w * n && hkeys[q] < hkeys[q - 1])
+                    return fail(ANOVA_ERR_CUDA, "plan check: keys not sorted");
+                if ((int)(hkeys[q] >> KB) != w) return fail(ANOVA_ERR_CUDA, "plan check: window order");
+            }
+        }
+        const int tw = B + 2 * m - 1;
+        for (int w = 0; w < P; ++w) {
+            const WindowInfo &wi = p->win[w];
+            int npts = 0;
+            for (int s2 = wi.seg_begin; s2 < wi.seg_end; ++s2) {
+                const int4 sg = segs[s2];
+                if (sg.w != w || sg.z < 1 || sg.z > kSegMax || sg.y < (long long)w * n ||
+                    (long long)sg.y + sg.z > (long long)(w + 1) * n)
+                    return fail(ANOVA_ERR_CUDA, "plan check: bad segment");
+                npts += sg.z;
+                for (int k = 0; k < 3; ++k) {
+                    const int c = (sg.x >> (10 * k)) & 1023;
+                    if (k < wi.dw ? (c - m + 1 < 0 || c + m > nos - 1) : c != 0)
+                        return fail(ANOVA_ERR_INVALID_ARG, "plan check: footprint leaves the grid");
+                }
+            }
+            if (npts != n) return fail(ANOVA_ERR_CUDA, "plan check: segments do not cover the points");
+            for (int x = wi.wi_begin; x < wi.wi_end; ++x) {
+                const int4 t = wis[x];
+                if (t.x != w || t.y < wi.seg_begin || t.z > wi.seg_end || t.y >= t.z)
+                    return fail(ANOVA_ERR_CUDA, "plan check: bad work item");
+                int pts = 0;
+                for (int s2 = t.y; s2 < t.z; ++s2) {
+                    pts += segs[s2].z;
+                    for (int k = 0; k < 3; ++k) {
+                        const int c = (segs[s2].x >> (10 * k)) & 1023, b = (t.w >> (10 * k)) & 1023;
+                        const int lc = c - b * B;
+                        if (k < wi.dw ? (lc < 0 || lc >= B || b * B - m + 1 < 0 || b * B + B + m - 1 > nos - 1)
+                                      : (c != 0 || b != 0))
+                            return fail(ANOVA_ERR_CUDA, "plan check: segment outside its bin");
+                    }
+                }
+                if (pts > kWiMax) return fail(ANOVA_ERR_CUDA, "plan check: work item too large");
+            }
+            int nbins = 1;
+            for (int k = 0; k < wi.dw; ++k) nbins *= NB;
+            for (int b = 0; b < nbins; ++b) {
+                const int2 be = bins[wi.bin_off + b];
+                if (be.y == 0) continue;
+                if (be.x < wi.wi_begin || be.x + be.y > wi.wi_end) return fail(ANOVA_ERR_CUDA, "plan check: bin table");
+            }
+            for (int k = 0; k < wi.dw; ++k)
+                if (wi.box_lo[k] < 0 || wi.box_hi[k] > nos || wi.box_lo[k] >= wi.box_hi[k])
+                    return fail(ANOVA_ERR_CUDA, "plan check: grid box");
+            (void)tw;
+        }
+        for (const int4 &t : ftiles)
+            if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || t.z + 32 > nos || t.w < 0 ||
+                t.w >= p->win[t.x].dw)
+                return fail(ANOVA_ERR_CUDA, "plan check: FFT tile");
+    }
+
+    // ------------------------------------------------------------------ upload tables
+    std::vector<DevWindow> hdw(P);
+    for (int w = 0; w < P; ++w) {
+        const WindowInfo &wi = p->win[w];
+        DevWindow &x = hdw[w];
+        std::memset(&x, 0, sizeof(x));
+        x.dw = wi.dw;
+        for (int k = 0; k < 3; ++k) { x.box_lo[k] = wi.box_lo[k]; x.box_hi[k] = wi.box_hi[k]; }
+        x.grid_off = wi.grid_off;
+        x.bin_off = wi.bin_off;
+    }
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> anova_status {
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(dst, bytes);
+        if (e != cudaSuccess) return fail(ANOVA_ERR_OOM, "device allocation failed");
+        p->static_bytes += (int64_t)bytes;
+        if (src) {
+            e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        return ANOVA_OK;
+    };
+    anova_status s;
+    if ((s = upload((void **)&p->segs, segs.data(), sizeof(int4) * segs.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->wis, wis.data(), sizeof(int4) * wis.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->bins, bins.data(), sizeof(int2) * bins.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->mbins, mbins.data(), sizeof(int4) * mbins.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
+    std::vector<float> f32;
+    if (prec == ANOVA_FP64) {
+        if ((s = upload(&p->D1br, d1br.data(), sizeof(double) * d1br.size())) != ANOVA_OK) return s;
+        if ((s = upload(&p->tw, twid.data(), sizeof(double) * twid.size())) != ANOVA_OK) return s;
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        f32.assign(d1br.begin(), d1br.end());
+        if ((s = upload(&p->D1br, f32.data(), sizeof(float) * f32.size())) != ANOVA_OK) return s;
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        f32.assign(twid.begin(), twid.end());
+        if ((s = upload(&p->tw, f32.data(), sizeof(float) * f32.size())) != ANOVA_OK) return s;
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    p->static_bytes += (int64_t)(es * 3 * total + sizeof(int) * total);
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = plan.release();
+    return ANOVA_OK;
+}
+
+}  // namespace anova

@@ -1,0 +1,244 @@
+"""Parity of the CUDA ANOVA-NFFT matvec with the FP64 oracle (Sec. 3, K v = sum_l K_l v).
+
+Bars: relative l2 error <= 1e-4 for the FP32 plan (N=32, m=4) and <= 1e-9 for the FP64 plan
+against the direct sum; the stage entry points against the oracle's plain NFFT stages."""
+import numpy as np
+import pytest
+
+from oracle import kernel as ok
+from oracle import nfft as on
+from synth import (config1, config2, matvec_vectors, subsample_rows, minmax_scale,
+                   consecutive_windows, SEED_BASE)
+
+from ._gpu_util import require_gpu, rel_l2, to_dev, from_dev
+
+pytestmark = pytest.mark.gpu
+
+FP32_BAR = 1e-4
+FP64_BAR = 1e-9
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+def _run(torch, ab, plan, V, dtype):
+    V = np.asarray(V)
+    nrhs = 1 if V.ndim == 1 else V.shape[1]
+    v = to_dev(torch, V, dtype)
+    out = torch.empty_like(v)
+    ab.anova_matvec(plan, v, out, nrhs)
+    torch.cuda.synchronize()
+    return from_dev(out)
+
+
+def test_config1_fp32_ten_vectors(env):
+    torch, ab = env
+    cfg = config1()
+    V = matvec_vectors(2000, 10, SEED_BASE + 1 + 100)
+    plan = ab.anova_nfft_plan(cfg["X"], cfg["windows"], cfg["sigma"], N=32, m=4, flags=ab.ANOVA_FP32)
+    got = _run(torch, ab, plan, V, torch.float32)
+    ref = ok.anova_matvec(cfg["X"], cfg["windows"], cfg["sigma"], V)
+    for r in range(10):
+        assert rel_l2(got[:, r], ref[:, r]) <= FP32_BAR
+
+
+def test_config1_fp64_precise_plan(env):
+    torch, ab = env
+    cfg = config1()
+    V = matvec_vectors(2000, 3, SEED_BASE + 1 + 100)
+    plan = ab.anova_nfft_plan(cfg["X"], cfg["windows"], cfg["sigma"], N=64, m=6, flags=ab.ANOVA_FP64)
+    got = _run(torch, ab, plan, V, torch.float64)
+    ref = ok.anova_matvec(cfg["X"], cfg["windows"], cfg["sigma"], V)
+    for r in range(3):
+        assert rel_l2(got[:, r], ref[:, r]) <= FP64_BAR
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_matches_plain_nfft_of_the_oracle(env, prec):
+    torch, ab = env
+    rng = np.random.default_rng(11)
+    X = minmax_scale(rng.standard_normal((500, 3)))
+    v = rng.standard_normal(500)
+    W = np.array([[0, 1, 2]])
+    if prec == "fp32":
+        plan = ab.anova_nfft_plan(X, W, 0.7, N=32, m=4, flags=ab.ANOVA_FP32)
+        got = _run(torch, ab, plan, v, torch.float32)
+        ref = on.nfft_fastsum(X, W, 0.7, 32, 4, v)
+        assert rel_l2(got, ref) <= 2e-6
+    else:
+        plan = ab.anova_nfft_plan(X, W, 0.7, N=32, m=4, flags=ab.ANOVA_FP64)
+        got = _run(torch, ab, plan, v, torch.float64)
+        ref = on.nfft_fastsum(X, W, 0.7, 32, 4, v)
+        assert rel_l2(got, ref) <= 1e-12
+
+
+def _small_plan(ab, prec, N=16, m=4, n=300, seed=5, dw=3):
+    rng = np.random.default_rng(seed)
+    X = minmax_scale(rng.standard_normal((n, dw)))
+    W = np.array([list(range(dw)) + [-1] * (3 - dw)])
+    flags = ab.ANOVA_FP64 if prec == "fp64" else ab.ANOVA_FP32
+    plan = ab.anova_nfft_plan(X, W, 0.8, N=N, m=m, flags=flags)
+    return X, W, plan, rng
+
+
+@pytest.mark.parametrize("dw", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_stage_spread(env, dw, prec):
+    torch, ab = env
+    X, W, plan, rng = _small_plan(ab, prec, dw=dw)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    v = rng.standard_normal(X.shape[0])
+    n_os = 32
+    grid = torch.empty((n_os,) * dw, dtype=dt, device="cuda")
+    ab.anova_spread_grid(plan, 0, to_dev(torch, v, dt), grid)
+    torch.cuda.synchronize()
+    ref = on.spread_grid(X[:, :dw], v, n_os, 4)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(grid.cpu().numpy().astype(np.float64) - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dw", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_stage_conv(env, dw, prec):
+    torch, ab = env
+    X, W, plan, rng = _small_plan(ab, prec, dw=dw)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    n_os = 32
+    g = rng.standard_normal((n_os,) * dw)
+    out = torch.empty((n_os,) * dw, dtype=dt, device="cuda")
+    ab.anova_conv_grid(plan, 0, torch.tensor(g, dtype=dt, device="cuda"), out)
+    torch.cuda.synchronize()
+    D1 = on.deconv_diag_1d(0.8, 16, 4, n_os, on.kb_beta())
+    ref = on.conv_grid(g, D1)
+    tol = 1e-11 if prec == "fp64" else 3e-6
+    assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dw", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_stage_interp(env, dw, prec):
+    torch, ab = env
+    X, W, plan, rng = _small_plan(ab, prec, dw=dw)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    n_os = 32
+    g = rng.standard_normal((n_os,) * dw)
+    f = torch.empty(X.shape[0], dtype=dt, device="cuda")
+    ab.anova_interp_grid(plan, 0, torch.tensor(g, dtype=dt, device="cuda"), f)
+    torch.cuda.synchronize()
+    ref = on.interp_grid(X[:, :dw], g, n_os, 4)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(from_dev(f) - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_mixed_window_sizes_and_per_window_scales(env):
+    torch, ab = env
+    rng = np.random.default_rng(21)
+    X = minmax_scale(rng.standard_normal((3000, 8)))
+    W = consecutive_windows(8)            # 3 + 3 + 2 features
+    W = np.concatenate([W, [[7, -1, -1]]])  # and a 1-D window
+    ell = np.array([0.5, 1.0, 2.0, 0.3])
+    eta = np.array([1.0, 0.5, 2.0, -0.25])
+    v = rng.standard_normal(3000)
+    plan = ab.anova_nfft_plan_ex(X, W, ell, eta, N=32, m=4, flags=ab.ANOVA_FP32)
+    got = _run(torch, ab, plan, v, torch.float32)
+    ref = ok.anova_matvec(X, W, ell, v, eta=eta)
+    assert rel_l2(got, ref) <= FP32_BAR
+    # each window alone
+    for l in range(4):
+        out = torch.empty(3000, dtype=torch.float32, device="cuda")
+        ab.anova_window_matvec(plan, l, to_dev(torch, v, torch.float32), out)
+        torch.cuda.synchronize()
+        refl = ok.anova_matvec(X, W[l:l + 1], ell[l], v, eta=eta[l:l + 1])
+        assert rel_l2(from_dev(out), refl) <= FP32_BAR
+
+
+def test_multi_rhs_equals_single_rhs_bitwise(env):
+    torch, ab = env
+    rng = np.random.default_rng(31)
+    X = minmax_scale(rng.standard_normal((20000, 6)))
+    W = consecutive_windows(6)
+    plan = ab.anova_nfft_plan(X, W, 1.0, N=32, m=4)
+    V = matvec_vectors(20000, 16, 7)
+    many = _run(torch, ab, plan, V, torch.float32)
+    for r in (0, 5, 15):
+        one = _run(torch, ab, plan, V[:, r], torch.float32)
+        assert np.array_equal(one, many[:, r])
+    # and 20 columns (more than one workspace chunk)
+    V20 = matvec_vectors(20000, 20, 8)
+    m20 = _run(torch, ab, plan, V20, torch.float32)
+    assert np.array_equal(m20[:, 19], _run(torch, ab, plan, V20[:, 19], torch.float32))
+
+
+def test_deterministic_and_host_entry_point(env):
+    torch, ab = env
+    cfg = config1()
+    v = matvec_vectors(2000, 1, 3)[:, 0]
+    p1 = ab.anova_nfft_plan(cfg["X"], cfg["windows"], 1.0)
+    p2 = ab.anova_nfft_plan(cfg["X"], cfg["windows"], 1.0)
+    a = _run(torch, ab, p1, v, torch.float32)
+    b = _run(torch, ab, p1, v, torch.float32)
+    c = _run(torch, ab, p2, v, torch.float32)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    vh = np.asfortranarray(v.astype(np.float32))
+    kh = np.zeros_like(vh)
+    ab.anova_matvec_host(p1, vh, kh, 1)
+    assert np.array_equal(kh.astype(np.float64), a)
+
+
+def test_edge_cases(env):
+    torch, ab = env
+    W = np.array([[0, 1, 2], [3, -1, -1]])
+    # n = 1: K v = P v
+    x1 = np.array([[0.1, -0.2, 0.2, 0.0]])
+    p = ab.anova_nfft_plan(x1, W, 1.0, flags=ab.ANOVA_FP64, N=64, m=6)
+    got = _run(torch, ab, p, np.array([1.5]), torch.float64)
+    assert abs(got[0] - 3.0) <= 1e-9 * 3.0
+    # all points coincident: every entry of K equals P
+    Xc = np.tile([[0.05, -0.1, 0.15, -0.2]], (257, 1))
+    v = np.random.default_rng(1).standard_normal(257)
+    p = ab.anova_nfft_plan(Xc, W, 0.5, flags=ab.ANOVA_FP64, N=64, m=6)
+    got = _run(torch, ab, p, v, torch.float64)
+    assert np.allclose(got, 2 * v.sum(), rtol=1e-9, atol=1e-9 * np.abs(v).sum())
+    # points exactly on grid nodes, on cell edges and on the box corners
+    nodes = (np.arange(-12, 13) / 64.0)[:, None]
+    Xe = np.concatenate([np.hstack([nodes] * 4), [[0.2, 0.2, -0.2, -0.2], [-0.2, -0.2, 0.2, 0.2]]])
+    v = np.random.default_rng(2).standard_normal(Xe.shape[0])
+    p = ab.anova_nfft_plan(Xe, W, 0.7, N=32, m=4)
+    got = _run(torch, ab, p, v, torch.float32)
+    assert rel_l2(got, ok.anova_matvec(Xe, W, 0.7, v)) <= FP32_BAR
+    # duplicate-heavy window: three binary features -> 8 distinct points
+    rng = np.random.default_rng(3)
+    Xb = minmax_scale(rng.integers(0, 2, size=(5000, 3)).astype(float))
+    v = rng.standard_normal(5000)
+    p = ab.anova_nfft_plan(Xb, np.array([[0, 1, 2]]), 1.0, N=32, m=4)
+    got = _run(torch, ab, p, v, torch.float32)
+    assert rel_l2(got, ok.anova_matvec(Xb, np.array([[0, 1, 2]]), 1.0, v)) <= FP32_BAR
+
+
+@pytest.mark.parametrize("sigma,rows", [(1.0, 5000), (0.5, 1000), (2.0, 1000)])
+def test_config2_full_size_sampled_rows(env, sigma, rows):
+    """n = 1e6, three 3-D windows: rel. l2 error on a seeded row subsample vs the direct sum."""
+    torch, ab = env
+    cfg = config2()
+    X, W = cfg["X"], cfg["windows"]
+    v = matvec_vectors(X.shape[0], 1, SEED_BASE + 2 + 100)[:, 0]
+    plan = ab.anova_nfft_plan(X, W, sigma, N=32, m=4)
+    got = _run(torch, ab, plan, v, torch.float32)
+    idx = subsample_rows(X.shape[0], rows, SEED_BASE + 2 + 200)
+    ref = ok.anova_matvec(X, W, sigma, v, rows=idx)
+    assert rel_l2(got[idx], ref) <= FP32_BAR
+
+
+def test_config2_sixteen_rhs_sampled_rows(env):
+    torch, ab = env
+    cfg = config2()
+    X, W = cfg["X"], cfg["windows"]
+    V = matvec_vectors(X.shape[0], 16, SEED_BASE + 2 + 100)
+    plan = ab.anova_nfft_plan(X, W, 1.0, N=32, m=4)
+    got = _run(torch, ab, plan, V, torch.float32)
+    idx = subsample_rows(X.shape[0], 300, SEED_BASE + 2 + 200)
+    ref = ok.anova_matvec(X, W, 1.0, V, rows=idx)
+    for r in range(16):
+        assert rel_l2(got[idx, r], ref[:, r]) <= FP32_BAR
