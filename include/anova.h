@@ -135,6 +135,28 @@ anova_status anova_spread_grid(anova_plan_t plan, int l, const void *v, void *gr
 anova_status anova_conv_grid(anova_plan_t plan, int l, const void *grid_in, void *grid_out);
 anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void *f);
 
+/*
+ * anova_spread_grid_noalloc -- anova_spread_grid (same kernels, same grid) without any device
+ * allocation in the call. The paper has no counterpart; this exists for callers that cannot
+ * allocate device memory when they call: processes whose device memory is entirely reserved
+ * up front by their own pool, and loops with a fixed time budget per call, where cudaMalloc
+ * (which may wait for the whole device to become idle) is not acceptable.
+ *
+ * Scratch: the spread kernel's partial tiles go to one static device array of 16 MiB that the
+ * library declares at file scope; every GPU that loads the library holds it until the process
+ * exits. The window's tiles must fit: a window needs (work items up to and including the window)
+ * x (B + 2m - 1)^{d_l} elements (B = 4 for FP32 plans, 2 for FP64); a larger requirement returns
+ * ANOVA_ERR_INVALID_ARG with the sizes in the message (use anova_spread_grid then). The call
+ * makes no cudaMalloc, cudaFree or other allocating call; it clears the caller's grid itself.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All calls share the one
+ * array, which keeps the last call's tiles: calls that can overlap on the GPU (different
+ * streams, plans or threads without ordering between them) race on it.
+ * Arguments and errors as anova_spread_grid.
+ */
+anova_status anova_spread_grid_noalloc(anova_plan_t plan, int l, const void *v, void *grid);
+
 /* Plan facts. Any output pointer may be NULL. device_bytes = device memory the plan holds. */
 anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
                              int64_t *device_bytes);

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "anova_spread_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
     "anova_conv_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
     "anova_interp_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "anova_spread_grid_noalloc": (_c_int, [_vp, _c_int, _vp, _vp]),
     "anova_plan_info": (_c_int, [_vp, _lp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                  ctypes.POINTER(_c_int), _lp]),
     "anova_plan_destroy": (None, [_vp]),
@@ -209,6 +210,11 @@ def anova_window_matvec(plan, l, v, Kv):
 
 def anova_spread_grid(plan, l, v, grid):
     _check(lib().anova_spread_grid(plan.handle, int(l), _dev_ptr(v), _dev_ptr(grid)))
+
+
+def anova_spread_grid_noalloc(plan, l, v, grid):
+    """anova_spread_grid without device allocation in the call (fixed 16 MiB static scratch)."""
+    _check(lib().anova_spread_grid_noalloc(plan.handle, int(l), _dev_ptr(v), _dev_ptr(grid)))
 
 
 def anova_conv_grid(plan, l, grid_in, grid_out):
