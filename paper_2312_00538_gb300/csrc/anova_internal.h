@@ -95,7 +95,9 @@ struct anova_plan {
 
     // device memory
     void *frac = nullptr;         // T[3][P*n]: fractional cell offsets, sorted per window
+    double *xw = nullptr;         // double[P][3][n]: window coordinates in original point order
     int32_t *perm = nullptr;      // [P*n]: sorted position -> original point index
+    unsigned char *cellloc = nullptr;  // [P*n]: cell index inside its bin, (l0 B + l1) B + l2
     int4 *segs = nullptr;         // {cell packed, sorted start, count, window}
     int4 *wis = nullptr;          // {window, seg_begin, seg_end, tile origin packed}
     int2 *bins = nullptr;         // per window per bin: {first work item, count}
@@ -112,6 +114,7 @@ struct anova_plan {
     void *grids = nullptr;        // T[4][ws_rhs][grid_total]
     void *tiles = nullptr;        // T[nwi][ws_rhs][tile_vol]
     void *part = nullptr;         // T[P][ws_rhs][n]
+    void *vsorted = nullptr;      // float[ws_rhs][P n]: v in sorted order (FP32 packed spread)
     int64_t ws_bytes = 0;
     // host-call staging
     void *dv = nullptr, *dkv = nullptr;

@@ -21,16 +21,24 @@ struct WinParams {
 template <typename T, int M>
 struct Weights;
 
+// The window is even, so the weight of offset 2M-1-j at z equals the weight of offset j at -z.
+// With p_j(z) = E_j(z^2) + z O_j(z^2), both come from one evaluation of E_j and O_j at z^2.
 template <int M>
 struct Weights<float, M> {
     static __device__ __forceinline__ void eval(float f, const WinParams &wp, float *w) {
+        static_assert(kPolyDeg % 2 == 1, "even/odd split assumes an odd degree");
         const float z = fmaf(2.0f, f, -1.0f);
+        const float z2 = z * z;
 #pragma unroll
-        for (int j = 0; j < 2 * M; ++j) {
-            float acc = wp.c[j][kPolyDeg];
+        for (int j = 0; j < M; ++j) {
+            float e = wp.c[j][kPolyDeg - 1], o = wp.c[j][kPolyDeg];
 #pragma unroll
-            for (int p = kPolyDeg - 1; p >= 0; --p) acc = fmaf(acc, z, wp.c[j][p]);
-            w[j] = acc;
+            for (int p = kPolyDeg - 3; p >= 0; p -= 2) {
+                e = fmaf(e, z2, wp.c[j][p]);
+                o = fmaf(o, z2, wp.c[j][p + 1]);
+            }
+            w[j] = fmaf(z, o, e);
+            w[2 * M - 1 - j] = fmaf(-z, o, e);
         }
     }
 };
@@ -60,6 +68,28 @@ struct Weights<double, M> {
 };
 
 __device__ __forceinline__ int cell_coord(int packed, int k) { return (packed >> (10 * k)) & 1023; }
+
+// ---------------------------------------------------------------- packed FP32 pairs (f32x2)
+// Blackwell executes fma/mul/add on two FP32 lanes per instruction; the FMA pipe rate in FLOP/s
+// is unchanged, but every instruction does two operations, which frees issue slots for the loads
+// that feed the spread and interpolation loops.
+typedef float2 f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+    lo = v.x;
+    hi = v.y;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f32x2 zero2() { return make_float2(0.0f, 0.0f); }
+// two pairs from one 16-byte aligned shared-memory load
+__device__ __forceinline__ void lds_pairs(const float *p, f32x2 &a, f32x2 &b) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+}
 
 // Load n contiguous T from 16-byte aligned shared memory.
 template <typename T, int CNT>

@@ -1,0 +1,549 @@
+// Low-rank kernel approximations and the Woodbury preconditioner (arXiv 2312.00538, Secs. 4-5).
+//
+//  * Algorithm 2 (greedy pivoted Cholesky) of K = sum_l K_l, column by column on the device in
+//    FP64: each column of K is evaluated from the plan's FP64 window coordinates (the kernel's
+//    definition, Sec. 3), the projection on the previous columns is removed, the residual
+//    diagonal is updated, and the next pivot is its arg-max (ties to the lowest index). The
+//    pivot never travels to the host during the build.
+//  * Nystrom (Sec. 4) on the pivoted columns S: K ~ K(:,S) K(S,S)^{-1} K(S,:), with the core
+//    factored as L D L^T and small D entries replaced by a threshold.
+//  * Woodbury (Sec. 5): A^ = Theta + Y L L^T Y, A^{-1} = Theta^{-1} - Theta^{-1} Y L M^{-1} L^T Y
+//    Theta^{-1}, M = I + L^T Theta^{-1} L (Y Theta^{-1} Y = Theta^{-1} since y_i^2 = 1). M is
+//    accumulated in FP64 from an FP32 copy of the n x r panel and factored by Cholesky on the
+//    device; the apply reads the FP32 panel twice.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "anova_internal.h"
+#include "lowrank_internal.h"
+
+namespace anova {
+namespace {
+
+struct KernParams {
+    int P;
+    int dw[kMaxWindows];
+    double inv_ell2[kMaxWindows];
+    double eta[kMaxWindows];
+};
+
+struct ValIdx {
+    double v;
+    long long i;
+};
+
+__device__ __forceinline__ ValIdx better(ValIdx a, ValIdx b) {
+    // larger value wins; equal values -> lower index
+    if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+    return a;
+}
+
+__device__ __forceinline__ ValIdx warp_argmax(ValIdx x) {
+    for (int o = 16; o > 0; o >>= 1) {
+        ValIdx y;
+        y.v = __shfl_down_sync(0xffffffffu, x.v, o);
+        y.i = __shfl_down_sync(0xffffffffu, x.i, o);
+        x = better(x, y);
+    }
+    return x;
+}
+
+// kernel entry K(i, p) from the FP64 window coordinates
+__device__ __forceinline__ double kernel_entry(const double *__restrict__ xw, long long n, long long i,
+                                               long long p, const KernParams &kp) {
+    double s = 0.0;
+    for (int w = 0; w < kp.P; ++w) {
+        double d2 = 0.0;
+        for (int k = 0; k < kp.dw[w]; ++k) {
+            const double *x = xw + ((long long)w * 3 + k) * n;
+            const double t = x[i] - x[p];
+            d2 += t * t;
+        }
+        s += kp.eta[w] * exp(-d2 * kp.inv_ell2[w]);
+    }
+    return s;
+}
+
+__global__ void k_fill(double *x, long long n, double v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// Column j of Algorithm 2: L(:, j) = (K(:, p) - L(:, :j) L(p, :j)^T) / sqrt(d_p), d -= L(:, j)^2,
+// and a per-block arg-max of the updated residual diagonal.
+__global__ void __launch_bounds__(256) k_pchol_column(int j, const double *__restrict__ xw, long long n,
+                                                      KernParams kp, double *__restrict__ L,
+                                                      double *__restrict__ d, const long long *__restrict__ piv,
+                                                      const double *__restrict__ dpiv, const int *__restrict__ stop,
+                                                      ValIdx *__restrict__ partial) {
+    extern __shared__ double lp[];
+    __shared__ ValIdx wbest[8];
+    if (*stop >= 0) return;  // the build already stopped at a smaller rank
+    const long long p = piv[j];
+    const double inv_sd = 1.0 / sqrt(dpiv[j]);
+    for (int q = threadIdx.x; q < j; q += blockDim.x) lp[q] = L[(long long)q * n + p];
+    __syncthreads();
+    ValIdx best{-INFINITY, (long long)1 << 62};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double col = kernel_entry(xw, n, i, p, kp);
+        for (int q = 0; q < j; ++q) col -= L[(long long)q * n + i] * lp[q];
+        const double lij = col * inv_sd;
+        L[(long long)j * n + i] = lij;
+        const double di = d[i] - lij * lij;
+        d[i] = di;
+        best = better(best, ValIdx{di, i});
+    }
+    best = warp_argmax(best);
+    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        ValIdx b = threadIdx.x < (blockDim.x >> 5) ? wbest[threadIdx.x] : ValIdx{-INFINITY, (long long)1 << 62};
+        b = warp_argmax(b);
+        if (threadIdx.x == 0) partial[blockIdx.x] = b;
+    }
+}
+
+// Next pivot = arg-max over the blocks' partials; stop when rank r is reached or the residual
+// diagonal is small (Algorithm 2: K_ll > 0 and r < k; tolerance err_tol * max diag).
+__global__ void k_pchol_pick(int j, int nparts, const ValIdx *__restrict__ partial, long long *piv,
+                             double *dpiv, int *stop, int rmax, double thresh) {
+    if (*stop >= 0) return;
+    ValIdx b{-INFINITY, (long long)1 << 62};
+    for (int t = threadIdx.x; t < nparts; t += 32) b = better(b, partial[t]);
+    b = warp_argmax(b);
+    if (threadIdx.x == 0) {
+        if (j + 1 >= rmax) {
+            *stop = j + 1;
+        } else if (!(b.v > thresh)) {
+            *stop = j + 1;
+        } else {
+            piv[j + 1] = b.i;
+            dpiv[j + 1] = b.v;
+        }
+    }
+}
+
+__global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long cnt) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------- Woodbury core
+// Partial Gram matrices of the scaled panel over row chunks: part[c](a, b) = sum_{i in chunk c}
+// L(i, a) L(i, b) / theta_i, for 32 x 32 tiles of the lower triangle, FP64 accumulation.
+constexpr int kCoreRows = 2048;
+
+__global__ void __launch_bounds__(256) k_core_partial(const float *__restrict__ L, const double *__restrict__ theta,
+                                                      long long n, int r, const int2 *__restrict__ tiles,
+                                                      double *__restrict__ part) {
+    __shared__ double A[32][33];
+    __shared__ double Bm[32][33];
+    const int2 t = tiles[blockIdx.x];
+    const int a0 = t.x * 32, b0 = t.y * 32;
+    const long long i0 = (long long)blockIdx.y * kCoreRows;
+    const long long i1 = min(n, i0 + kCoreRows);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
+    double acc[4] = {0, 0, 0, 0};
+    for (long long ib = i0; ib < i1; ib += 32) {
+        // stage 32 rows of the a-columns (scaled by 1/theta) and the b-columns
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int rr = e & 31, cc = e >> 5;
+            const long long i = ib + rr;
+            double va = 0.0, vb = 0.0;
+            if (i < i1) {
+                const double it = 1.0 / theta[i];
+                if (a0 + cc < r) va = (double)L[(long long)(a0 + cc) * n + i] * it;
+                if (b0 + cc < r) vb = (double)L[(long long)(b0 + cc) * n + i];
+            }
+            A[cc][rr] = va;
+            Bm[cc][rr] = vb;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            const double vb = Bm[tx][rr];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(A[ty + 8 * q][rr], vb, acc[q]);
+        }
+        __syncthreads();
+    }
+    const int ntiles = gridDim.x;
+    for (int q = 0; q < 4; ++q) {
+        const int aa = ty + 8 * q;
+        part[(((long long)blockIdx.y * ntiles + blockIdx.x) * 32 + aa) * 32 + tx] = acc[q];
+    }
+}
+
+// M = I + sum over chunks (fixed order), written as a full symmetric r x r matrix.
+__global__ void k_core_sum(const double *__restrict__ part, int nchunks, int ntiles,
+                           const int2 *__restrict__ tiles, int r, double *__restrict__ M) {
+    const int tile = blockIdx.x;
+    const int2 t = tiles[tile];
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int aa = e >> 5, bb = e & 31;
+        const int a = t.x * 32 + aa, b = t.y * 32 + bb;
+        if (a >= r || b >= r) continue;
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c) s += part[(((long long)c * ntiles + tile) * 32 + aa) * 32 + bb];
+        if (a == b) s += 1.0;
+        M[(long long)a * r + b] = s;
+        M[(long long)b * r + a] = s;
+    }
+}
+
+// In-place Cholesky of the SPD r x r matrix M (row-major, lower factor kept), one CTA.
+// Sets *info = 0 on success, k + 1 if the k-th pivot is not positive.
+__global__ void __launch_bounds__(1024) k_cholesky(double *M, int r, int *info) {
+    __shared__ double piv;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            const double dk = M[(long long)k * r + k];
+            if (!(dk > 0.0)) bad = k + 1;
+            piv = sqrt(dk > 0.0 ? dk : 1.0);
+            M[(long long)k * r + k] = piv;
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) M[(long long)i * r + k] /= piv;
+        __syncthreads();
+        const int m = r - k - 1;
+        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+            const int i = k + 1 + (int)(e / m), jj = k + 1 + (int)(e % m);
+            if (jj <= i) M[(long long)i * r + jj] -= M[(long long)i * r + k] * M[(long long)jj * r + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *info = bad;
+}
+
+// Solve (R R^T) z = u with the lower factor R (row-major), one CTA, in place in z.
+__global__ void __launch_bounds__(1024) k_chol_solve(const double *__restrict__ R, int r, double *z) {
+    for (int k = 0; k < r; ++k) {  // forward: R w = u
+        __syncthreads();
+        if (threadIdx.x == 0) z[k] /= R[(long long)k * r + k];
+        __syncthreads();
+        const double zk = z[k];
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) z[i] -= R[(long long)i * r + k] * zk;
+    }
+    for (int k = r - 1; k >= 0; --k) {  // backward: R^T z = w
+        __syncthreads();
+        if (threadIdx.x == 0) z[k] /= R[(long long)k * r + k];
+        __syncthreads();
+        const double zk = z[k];
+        for (int i = threadIdx.x; i < k; i += blockDim.x) z[i] -= R[(long long)k * r + i] * zk;
+    }
+}
+
+// u_part[c](q) = sum_{i in chunk c} L(i, q) t_i with t = y .* g ./ theta; one warp per column,
+// lanes over the chunk's rows.
+constexpr int kApplyRows = 8192;
+
+__global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, const double *__restrict__ theta,
+                                                 const double *__restrict__ y, const double *__restrict__ g,
+                                                 long long n, int r, double *__restrict__ upart) {
+    const long long i0 = (long long)blockIdx.x * kApplyRows;
+    const long long i1 = min(n, i0 + kApplyRows);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < r; q += blockDim.x >> 5) {
+        const float *col = L + (long long)q * n;
+        double s = 0.0;
+        for (long long i = i0 + lane; i < i1; i += 32) s += (double)col[i] * (y[i] * g[i] / theta[i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) upart[(long long)blockIdx.x * r + q] = s;
+    }
+}
+
+__global__ void k_panel_t_sum(const double *__restrict__ upart, int nchunks, int r, double *__restrict__ u) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r; q += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c) s += upart[(long long)c * r + q];
+        u[q] = s;
+    }
+}
+
+// x_i = g_i / theta_i - (y_i / theta_i) sum_q L(i, q) z_q for i < n; x_n = g_n / s_schur.
+__global__ void __launch_bounds__(256) k_panel_n(const float *__restrict__ L, const double *__restrict__ theta,
+                                                 const double *__restrict__ y, const double *__restrict__ g,
+                                                 const double *__restrict__ z, long long n, int r,
+                                                 double *__restrict__ x, const double *__restrict__ schur) {
+    extern __shared__ double zs[];
+    for (int q = threadIdx.x; q < r; q += blockDim.x) zs[q] = z[q];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < r; ++q) s += (double)L[(long long)q * n + i] * zs[q];
+        const double it = 1.0 / theta[i];
+        x[i] = g[i] * it - y[i] * it * s;
+    }
+    if (schur && blockIdx.x == 0 && threadIdx.x == 0) x[n] = g[n] / *schur;
+}
+
+// s = y^T A^{-1} y from the Woodbury apply of y (partial dots, then one block)
+__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, long long n,
+                              double *__restrict__ part) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_parts(const double *__restrict__ part, int np, double *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+// Nystrom core on the pivot set: C = K(S, S) (r x r), then L <- L_S-based factor. With the
+// pivoted-Cholesky columns, K(:, S) = L R^T where R = L(S, :) (lower triangular in pivot order),
+// so C = R R^T and K(:,S) C^{-1} K(S,:) = L L^T: the Nystrom approximation on S equals the
+// pivoted-Cholesky one. The L D L^T route of Sec. 4 is therefore applied to C directly and the
+// factor Z = K(:, S) L_C^{-T} D^{-1/2} replaces L.
+__global__ void k_gather_core(const double *__restrict__ xw, long long n, KernParams kp,
+                              const long long *__restrict__ piv, int r, double *__restrict__ C) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int a = e / r, b = e % r;
+        C[e] = kernel_entry(xw, n, piv[a], piv[b], kp);
+    }
+}
+
+// L D L^T without pivoting, one CTA, in place (unit lower factor below the diagonal, D on it);
+// D entries below thresh are replaced by thresh.
+__global__ void __launch_bounds__(1024) k_ldl(double *C, int r, double rel_thresh) {
+    __shared__ double dk_s, thr;
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int k = 0; k < r; ++k) mx = fmax(mx, fabs(C[(long long)k * r + k]));
+        thr = rel_thresh * mx;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            double dk = C[(long long)k * r + k];
+            if (dk < thr) dk = thr;
+            C[(long long)k * r + k] = dk;
+            dk_s = dk;
+        }
+        __syncthreads();
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) C[(long long)i * r + k] /= dk_s;
+        __syncthreads();
+        const int m = r - k - 1;
+        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
+            const int i = k + 1 + (int)(e / m), jj = k + 1 + (int)(e % m);
+            if (jj <= i) C[(long long)i * r + jj] -= C[(long long)i * r + k] * C[(long long)jj * r + k] * dk_s;
+        }
+        __syncthreads();
+    }
+}
+
+// Z(:, q) for the Nystrom factor: row i solves L_C z^T = K(S, i) forward, then scales by D^{-1/2}.
+__global__ void __launch_bounds__(128) k_nystrom_rows(const double *__restrict__ xw, long long n, KernParams kp,
+                                                      const long long *__restrict__ piv, const double *__restrict__ C,
+                                                      int r, double *__restrict__ Z) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        for (int a = 0; a < r; ++a) {
+            double s = kernel_entry(xw, n, i, piv[a], kp);
+            for (int b = 0; b < a; ++b) s -= C[(long long)a * r + b] * Z[(long long)b * n + i];
+            Z[(long long)a * n + i] = s;
+        }
+        for (int a = 0; a < r; ++a) Z[(long long)a * n + i] /= sqrt(C[(long long)a * r + a]);
+    }
+}
+
+KernParams kern_params(const anova_plan *p) {
+    KernParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.P = p->P;
+    for (int w = 0; w < p->P; ++w) {
+        kp.dw[w] = p->win[w].dw;
+        kp.inv_ell2[w] = 1.0 / (p->win[w].ell * p->win[w].ell);
+        kp.eta[w] = p->win[w].eta;
+    }
+    return kp;
+}
+
+int grid_for(long long n, int threads, int cap = 152 * 8) {
+    return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+void lowrank_release(lowrank *lr) {
+    if (!lr) return;
+    void *bufs[] = {lr->L64, lr->L32, lr->d, lr->piv_dev, lr->dpiv, lr->stop, lr->partial, lr->M,
+                    lr->u, lr->upart, lr->tiles, lr->cpart, lr->info, lr->tmp, lr->dpart, lr->schur};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete lr;
+}
+
+anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, uint64_t seed, lowrank **out) {
+    if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+    if (kind != PCHOL_GREEDY && kind != NYSTROM) return fail(ANOVA_ERR_INVALID_ARG, "unknown preconditioner kind");
+    if (r < 1 || r > 1024) return fail(ANOVA_ERR_INVALID_ARG, "rank must be in [1, 1024]");
+    if (!(err_tol >= 0.0) || !std::isfinite(err_tol)) return fail(ANOVA_ERR_INVALID_ARG, "err_tol must be >= 0");
+    for (int w = 0; w < p->P; ++w)
+        if (p->win[w].eta < 0) return fail(ANOVA_ERR_INVALID_ARG, "low-rank factors need eta_l >= 0 (K must be PSD)");
+    (void)seed;
+    const long long n = p->n;
+    r = (int)std::min<long long>(r, n);
+    lowrank *lr = new (std::nothrow) lowrank();
+    if (!lr) return fail(ANOVA_ERR_OOM, "host allocation failed");
+    lr->plan = p;
+    lr->kind = kind;
+    lr->rmax = r;
+    lr->n = n;
+    cudaStream_t st = p->stream;
+    const int nb = grid_for(n, 256, 152 * 4);
+    cudaError_t e;
+    auto bail = [&](anova_status s) {
+        lowrank_release(lr);
+        return s;
+    };
+    if ((e = cudaMalloc(&lr->L64, sizeof(double) * n * r)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->d, sizeof(double) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->piv_dev, sizeof(long long) * (r + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&lr->dpiv, sizeof(double) * (r + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&lr->stop, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&lr->partial, 16 * (size_t)nb)) != cudaSuccess)
+        return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    const KernParams kp = kern_params(p);
+    double diag = 0.0;
+    for (int w = 0; w < p->P; ++w) diag += p->win[w].eta;   // K_ii = sum_l eta_l
+    if (!(diag > 0.0)) return bail(fail(ANOVA_ERR_INVALID_ARG, "kernel diagonal is not positive"));
+    k_fill<<<nb, 256, 0, st>>>(lr->d, n, diag);
+    const long long zero = 0;
+    const int minus1 = -1;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->piv_dev, &zero, sizeof(long long), cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->dpiv, &diag, sizeof(double), cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->stop, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+    const double thresh = err_tol * diag;
+    for (int j = 0; j < r; ++j) {
+        k_pchol_column<<<nb, 256, sizeof(double) * std::max(1, j), st>>>(
+            j, p->xw, n, kp, lr->L64, lr->d, (const long long *)lr->piv_dev, lr->dpiv, lr->stop,
+            (ValIdx *)lr->partial);
+        k_pchol_pick<<<1, 32, 0, st>>>(j, nb, (const ValIdx *)lr->partial, (long long *)lr->piv_dev,
+                                       lr->dpiv, lr->stop, r, thresh);
+    }
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    int rank = 0;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(&rank, lr->stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<long long> piv(r);
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(piv.data(), lr->piv_dev, sizeof(long long) * r, cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rank < 1 || rank > r) return bail(fail(ANOVA_ERR_CUDA, "pivoted Cholesky returned no rank"));
+    lr->rank = rank;
+    lr->piv.assign(piv.begin(), piv.begin() + rank);
+    if (kind == NYSTROM) {
+        // classic Nystrom on the pivot set with the L D L^T core (Sec. 4)
+        double *C = nullptr;
+        if ((e = cudaMalloc(&C, sizeof(double) * rank * rank)) != cudaSuccess)
+            return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+        k_gather_core<<<grid_for((long long)rank * rank, 256), 256, 0, st>>>(p->xw, n, kp,
+                                                                            (const long long *)lr->piv_dev, rank, C);
+        k_ldl<<<1, 1024, 0, st>>>(C, rank, 1e-10);
+        k_nystrom_rows<<<grid_for(n, 128, 152 * 16), 128, 0, st>>>(p->xw, n, kp, (const long long *)lr->piv_dev,
+                                                                    C, rank, lr->L64);
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(C);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "Nystrom kernels"));
+        if (e2 != cudaSuccess) return bail(cuda_fail(e2, "Nystrom sync"));
+    }
+    if ((e = cudaMalloc(&lr->L32, sizeof(float) * n * rank)) != cudaSuccess)
+        return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    k_to_float<<<grid_for(n * rank, 256), 256, 0, st>>>(lr->L64, lr->L32, n * rank);
+    // Woodbury workspace
+    const int nt = (rank + 31) / 32;
+    std::vector<int2> tiles;
+    for (int a = 0; a < nt; ++a)
+        for (int b = 0; b <= a; ++b) tiles.push_back(make_int2(a, b));
+    lr->ntiles = (int)tiles.size();
+    lr->nchunks = (int)((n + kCoreRows - 1) / kCoreRows);
+    lr->napply = (int)((n + kApplyRows - 1) / kApplyRows);
+    if ((e = cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->upart, sizeof(double) * rank * lr->napply)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->tiles, sizeof(int2) * tiles.size())) != cudaSuccess ||
+        (e = cudaMalloc(&lr->cpart, sizeof(double) * 1024 * tiles.size() * lr->nchunks)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->info, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&lr->tmp, sizeof(double) * (n + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&lr->dpart, sizeof(double) * 1024)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->schur, sizeof(double))) != cudaSuccess)
+        return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = lr;
+    return ANOVA_OK;
+}
+
+// Woodbury apply of the (n x n) block: x[0:n] = A^{-1} g[0:n]; if with_schur, x[n] = g[n]/s.
+anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, const double *g, double *x,
+                            bool with_schur) {
+    anova_plan *p = lr->plan;
+    cudaStream_t st = p->stream;
+    const long long n = lr->n;
+    const int r = lr->rank;
+    k_panel_t<<<lr->napply, 256, 0, st>>>(lr->L32, theta, y, g, n, r, lr->upart);
+    k_panel_t_sum<<<grid_for(r, 128), 128, 0, st>>>(lr->upart, lr->napply, r, lr->u);
+    k_chol_solve<<<1, 1024, 0, st>>>(lr->M, r, lr->u);
+    k_panel_n<<<grid_for(n, 256, 152 * 8), 256, sizeof(double) * r, st>>>(lr->L32, theta, y, g, lr->u, n, r, x,
+                                                                          with_schur ? lr->schur : nullptr);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    return ANOVA_OK;
+}
+
+anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const double *y) {
+    anova_plan *p = lr->plan;
+    cudaStream_t st = p->stream;
+    const long long n = lr->n;
+    const int r = lr->rank;
+    k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, theta, n, r, (const int2 *)lr->tiles,
+                                                                   lr->cpart);
+    k_core_sum<<<lr->ntiles, 256, 0, st>>>(lr->cpart, lr->nchunks, lr->ntiles, (const int2 *)lr->tiles, r, lr->M);
+    k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    int info = 0;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info != 0) return fail(ANOVA_ERR_BREAKDOWN, "Woodbury core is not positive definite");
+    // Schur complement s = y^T A^{-1} y of the block preconditioner
+    anova_status s = woodbury_apply(lr, theta, y, y, lr->tmp, false);
+    if (s != ANOVA_OK) return s;
+    const int nb = grid_for(n, 256, 1024);
+    k_dot_partial<<<nb, 256, 0, st>>>(y, lr->tmp, n, lr->dpart);
+    k_sum_parts<<<1, 32, 0, st>>>(lr->dpart, nb, lr->schur);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    double sv = 0.0;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(&sv, lr->schur, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(sv > 0.0) || !std::isfinite(sv)) return fail(ANOVA_ERR_BREAKDOWN, "y^T A^{-1} y is not positive");
+    lr->schur_host = sv;
+    lr->core_ready = true;
+    return ANOVA_OK;
+}
+
+anova_status lowrank_apply_impl(lowrank *lr, const double *theta, const double *y, const double *g, double *x) {
+    if (!lr->core_ready) return fail(ANOVA_ERR_INVALID_ARG, "call lowrank_precond_set_theta first");
+    return woodbury_apply(lr, theta, y, g, x, true);
+}
+
+}  // namespace anova

@@ -1,0 +1,39 @@
+// Internal layout of a low-rank preconditioner (not part of the C ABI).
+#pragma once
+
+#include <vector>
+
+#include "anova_internal.h"
+
+struct lowrank {
+    anova_plan *plan = nullptr;  // not owned: the plan must outlive the preconditioner
+    int kind = 0, rmax = 0, rank = 0;
+    long long n = 0;
+    std::vector<long long> piv;  // pivots in the order chosen
+    double *L64 = nullptr;       // n x rmax, column-major, FP64 factor (K ~ L L^T)
+    float *L32 = nullptr;        // n x rank, column-major FP32 panel used by the Woodbury steps
+    double *d = nullptr;         // residual diagonal during the build
+    void *piv_dev = nullptr;     // long long[rmax + 1]
+    double *dpiv = nullptr;
+    int *stop = nullptr;
+    void *partial = nullptr;
+    // Woodbury core
+    double *M = nullptr;         // rank x rank, Cholesky factor after set_theta
+    double *u = nullptr, *upart = nullptr;
+    void *tiles = nullptr;
+    double *cpart = nullptr;
+    int *info = nullptr;
+    double *tmp = nullptr, *dpart = nullptr, *schur = nullptr;
+    int ntiles = 0, nchunks = 0, napply = 0;
+    double schur_host = 0.0;
+    bool core_ready = false;
+};
+
+namespace anova {
+anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, uint64_t seed, lowrank **out);
+anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const double *y);
+anova_status lowrank_apply_impl(lowrank *lr, const double *theta, const double *y, const double *g, double *x);
+anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, const double *g, double *x,
+                            bool with_schur);
+void lowrank_release(lowrank *lr);
+}  // namespace anova

@@ -71,6 +71,41 @@ cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t 
     return cudaGetLastError();
 }
 
+template <int M>
+cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
+    constexpr int B = Prec<float>::B, NW = Prec<float>::SPREAD_WARPS;
+    using C = SpreadX2Cfg<M, B, NW>;
+    auto kern = k_spread3_x2<M, B, NW>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_interp3_x2(const InterpWiArgs &a, int nblocks, int nrhs, cudaStream_t st) {
+    constexpr int B = Prec<float>::B, NW = Prec<float>::INTERP_WARPS;
+    using C = InterpX2Cfg<M, B, NW>;
+    auto kern = k_interp3_x2<M, B, NW>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// the FP32 3-D paths with a packed kernel (footprint edge 2m divides 16)
+inline bool packed_path(int prec_bytes, int dw, int m) { return prec_bytes == 4 && dw == 3 && (m == 2 || m == 4); }
+
 // runtime (dw, m) -> template dispatch
 template <typename T, int DW>
 cudaError_t dispatch_spread_m(int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
@@ -95,6 +130,11 @@ cudaError_t dispatch_spread_m(int m, const SpreadArgs &a, int nb, int nrhs, cuda
 
 template <typename T>
 cudaError_t dispatch_spread(int dw, int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        // the packed kernel reads v in sorted order; callers without that copy use the generic one
+        if (a.vsorted && dw == 3 && m == 4) return launch_spread3_x2<4>(a, nb, nrhs, st);
+        if (a.vsorted && dw == 3 && m == 2) return launch_spread3_x2<2>(a, nb, nrhs, st);
+    }
     switch (dw) {
         case 1: return dispatch_spread_m<T, 1>(m, a, nb, nrhs, st);
         case 2: return dispatch_spread_m<T, 2>(m, a, nb, nrhs, st);
@@ -186,8 +226,10 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
     ba.mb_begin = p->win[a0].mb_begin;
     ba.nmbins = p->win[a1 - 1].mb_end - ba.mb_begin;
     ba.nrhs = nrhs;
+    ba.tv_max = tile_volume<T>(p, dw);
     if (ba.nmbins > 0) {
-        k_bin_reduce<T><<<dim3(ba.nmbins, nrhs), 256, 0, st>>>(ba);
+        const int chunks = (ba.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
+        k_bin_reduce<T><<<dim3(ba.nmbins * chunks, nrhs), 256, 0, st>>>(ba);
         ANOVA_CUDA_TRY(cudaGetLastError());
         p->launches += 1;
     }
@@ -231,8 +273,20 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         if (a0 >= a1) continue;
         const int wi0 = p->win[a0].wi_begin, wi1 = p->win[a1 - 1].wi_end;
         const int s0 = p->win[a0].seg_begin, s1 = p->win[a1 - 1].seg_end;
+        const bool packed = packed_path((int)sizeof(T), gr.dw, p->m);
+        cudaEvent_t e0 = stage_event(p);
+        if (packed) {
+            // v in sorted order for the packed spread
+            const long long q0 = (long long)a0 * p->n, q1 = (long long)a1 * p->n;
+            const int nb = (int)std::min<long long>(((q1 - q0) * nrhs + 255) / 256, 152LL * 16);
+            k_gather_v<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float *>(v), p->perm, p->n, p->n * p->P, q0, q1,
+                                           nrhs, reinterpret_cast<float *>(p->vsorted));
+            ANOVA_CUDA_TRY(cudaGetLastError());
+            p->launches += 1;
+        }
         // 1. spread into partial tiles
         SpreadArgs sa;
+        sa.vsorted = packed ? p->vsorted : nullptr;
         sa.wis = p->wis;
         sa.segs = p->segs;
         sa.frac = p->frac;
@@ -245,7 +299,6 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         sa.wi_begin = wi0;
         sa.wi_end = wi1;
         sa.wp = wp;
-        cudaEvent_t e0 = stage_event(p);
         if (wi1 > wi0) {
             cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "spread launch");
@@ -300,7 +353,30 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         ia.zero_offset = 0;
         ia.part_w0 = w0;
         ia.wp = wp;
-        if (s1 > s0) {
+        if (packed && wi1 > wi0) {
+            InterpWiArgs xa;
+            xa.wis = p->wis;
+            xa.segs = p->segs;
+            xa.frac = reinterpret_cast<const float *>(p->frac);
+            xa.perm = p->perm;
+            xa.cellloc = p->cellloc;
+            xa.grid = reinterpret_cast<const float *>(g[3]);
+            xa.dwin = p->dwin;
+            xa.part = reinterpret_cast<float *>(part);
+            xa.n = p->n;
+            xa.total = p->n * p->P;
+            xa.grid_stride_rhs = grid_stride;
+            xa.nrhs = nrhs;
+            xa.wi_begin = wi0;
+            xa.wi_end = wi1;
+            xa.n_os = p->n_os;
+            xa.part_w0 = w0;
+            xa.wp = wp;
+            cudaError_t e = p->m == 4 ? launch_interp3_x2<4>(xa, wi1 - wi0, nrhs, st)
+                                      : launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
+            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+            p->launches += 1;
+        } else if (s1 > s0) {
             cudaError_t e = dispatch_interp<T>(gr.dw, p->m, ia, s1 - s0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "interp launch");
             p->launches += 1;

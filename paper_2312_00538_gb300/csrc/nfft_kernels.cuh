@@ -17,6 +17,7 @@
 namespace anova {
 
 struct SpreadArgs {
+    const void *vsorted;    // FP32 packed path: v gathered into sorted order, [nrhs][total]
     const int4 *wis;        // {window, seg_begin, seg_end, bin packed}
     const int4 *segs;       // {cell packed, sorted start, count, window}
     const void *frac;       // T[3][total]
@@ -167,6 +168,231 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ FP32 3-D spread, packed
+// Specialisation of k_spread for FP32 3-D windows whose footprint edge 2M divides 16 (M = 2, 4):
+// a half-warp owns one point at a time, each lane holds 16/(2M) x ... rows (a, b) of the
+// footprint -- (2M)^2 / 16 rows of 2M values -- as f32x2 pairs along c, so the warp advances two
+// points per step with fma.rn.f32x2. The staged weights are laid out so that every load is a
+// 64- or 128-bit broadcast: X duplicated into pairs and permuted so that a lane's rows are
+// contiguous, Y duplicated into pairs, Z (times v) plain.
+template <int M, int B, int NWARP>
+struct SpreadX2Cfg {
+    static constexpr int W2 = 2 * M;
+    static constexpr int RPL = W2 * W2 / 16;         // rows per lane
+    static constexpr int S = 16 / W2;                // a-stride between a lane's rows
+    static constexpr int TW = B + W2 - 1;
+    static constexpr int TV = TW * TW * TW;
+    static constexpr int TVP = (TV + 3) / 4 * 4;
+    static constexpr int XO = 0, YO = 2 * W2, ZO = 4 * W2, PS = 5 * W2;  // staged floats per point
+    static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS);
+};
+
+template <int M, int B, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32) k_spread3_x2(SpreadArgs a) {
+    using C = SpreadX2Cfg<M, B, NWARP>;
+    constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
+    static_assert(16 % W2 == 0 && RPL * 16 == W2 * W2, "2M must divide 16");
+    static_assert(W2 % 4 == 0 && (RPL % 2 == 0 || RPL == 1), "vector staging layout");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tiles_s = reinterpret_cast<float *>(smem_raw);
+    float *wts_s = tiles_s + NWARP * C::TVP;
+
+    const int wi_idx = a.wi_begin + blockIdx.x;
+    if (wi_idx >= a.wi_end) return;
+    const int r = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = lane >> 4, lh = lane & 15;
+    const int4 wi = a.wis[wi_idx];
+    const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
+
+    for (int i = threadIdx.x; i < NWARP * C::TVP; i += NWARP * 32) tiles_s[i] = 0.0f;
+    __syncthreads();
+
+    // each warp takes whole cells: the segments starting in its share of the item's points
+    // (split at segment boundaries, so no cell is divided between warps)
+    const int4 s_first = a.segs[wi.y];
+    const int4 s_last = a.segs[wi.z - 1];
+    const int p0 = s_first.y, p1 = s_last.y + s_last.z;
+    const int len = p1 - p0;
+    auto first_seg_from = [&](int target) {
+        int lo = wi.y, hi = wi.z;  // first segment with start >= target (wi.z if none)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.segs[mid].y >= target) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    const int sw0 = warp == 0 ? wi.y : first_seg_from(p0 + (int)(((long long)len * warp) / NWARP));
+    const int sw1 = warp == NWARP - 1 ? wi.z : first_seg_from(p0 + (int)(((long long)len * (warp + 1)) / NWARP));
+    const int pw0 = sw0 < wi.z ? a.segs[sw0].y : p1;
+    const int pw1 = sw1 < wi.z ? a.segs[sw1].y : p1;
+
+    const float *fr0 = reinterpret_cast<const float *>(a.frac);
+    const float *fr1 = fr0 + a.total, *fr2 = fr0 + 2 * a.total;
+    const float *vs = reinterpret_cast<const float *>(a.vsorted) + (size_t)r * a.total;
+    float *tile = tiles_s + warp * C::TVP;
+    float *wts = wts_s + warp * 32 * PS;
+    const int g = lh / W2;           // this lane's rows: a = g + S k, b = lh % W2
+    const int rb = lh % W2;
+
+    if (pw0 < pw1) {
+        int s = sw0;
+        int4 sg = a.segs[s];
+        int4 sg_next = (s + 1 < wi.z) ? a.segs[s + 1] : sg;
+        int q = pw0;
+        int send = min(sg.y + sg.z, pw1);
+        int cnt = min(32, send - q);
+        // per-point inputs of the current batch (prefetched one batch ahead)
+        float fx = 0.f, fy = 0.f, fz = 0.f, vv = 0.f;
+        if (lane < cnt) {
+            fx = fr0[q + lane];
+            fy = fr1[q + lane];
+            fz = fr2[q + lane];
+            vv = vs[q + lane];
+        }
+        f32x2 acc[RPL][W2 / 2];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k)
+#pragma unroll
+            for (int c = 0; c < W2 / 2; ++c) acc[k][c] = zero2();
+        while (true) {
+            // next batch: same piece, or the first batch of the next segment in range
+            const int qn = q + cnt;
+            bool newpiece = false, done = false;
+            int sn = s, sendn = send;
+            int4 sgn = sg;
+            if (qn >= send) {
+                newpiece = true;
+                if (qn < pw1 && s + 1 < wi.z) {
+                    sn = s + 1;
+                    sgn = sg_next;
+                    sendn = min(sgn.y + sgn.z, pw1);
+                } else {
+                    done = true;
+                }
+            }
+            const int cntn = done ? 0 : min(32, sendn - qn);
+            float nfx = 0.f, nfy = 0.f, nfz = 0.f, nvv = 0.f;
+            if (lane < cntn) {
+                nfx = fr0[qn + lane];
+                nfy = fr1[qn + lane];
+                nfz = fr2[qn + lane];
+                nvv = vs[qn + lane];
+            }
+            int4 sg_next2 = sg_next;
+            if (newpiece && !done && sn + 1 < wi.z) sg_next2 = a.segs[sn + 1];
+            // stage the current batch's weights (zeros for lanes past the batch)
+            {
+                float wx[W2], wy[W2], wz[W2];
+                Weights<float, M>::eval(fx, a.wp, wx);
+                Weights<float, M>::eval(fy, a.wp, wy);
+                Weights<float, M>::eval(fz, a.wp, wz);
+                const float vl = lane < cnt ? vv : 0.0f;
+#pragma unroll
+                for (int j = 0; j < W2; ++j) wz[j] *= vl;
+                float4 *dst = reinterpret_cast<float4 *>(wts + lane * PS);
+#pragma unroll
+                for (int pos = 0; pos < W2; pos += 2) {
+                    const int a0 = (pos % RPL) * S + pos / RPL, a1 = ((pos + 1) % RPL) * S + (pos + 1) / RPL;
+                    dst[(C::XO / 4) + pos / 2] = make_float4(wx[a0], wx[a0], wx[a1], wx[a1]);
+                }
+#pragma unroll
+                for (int b = 0; b < W2; b += 2) dst[(C::YO / 4) + b / 2] = make_float4(wy[b], wy[b], wy[b + 1], wy[b + 1]);
+#pragma unroll
+                for (int c = 0; c < W2; c += 4) dst[(C::ZO / 4) + c / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
+            }
+            __syncwarp();
+            const int npair = (cnt + 1) >> 1;
+#pragma unroll 2
+            for (int jj = 0; jj < npair; ++jj) {
+                const float *pw = wts + (2 * jj + half) * PS;
+                f32x2 xr[RPL], z2[W2 / 2];
+                const f32x2 y2 = *reinterpret_cast<const f32x2 *>(pw + C::YO + 2 * rb);
+#pragma unroll
+                for (int k = 0; k < RPL; k += 2) {
+                    if (k + 1 < RPL) lds_pairs(pw + C::XO + 2 * (g * RPL + k), xr[k], xr[k + 1]);
+                    else xr[k] = *reinterpret_cast<const f32x2 *>(pw + C::XO + 2 * (g * RPL + k));
+                }
+#pragma unroll
+                for (int c = 0; c < W2 / 2; c += 2) lds_pairs(pw + C::ZO + 2 * c, z2[c], z2[c + 1]);
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const f32x2 rw = mul2(xr[k], y2);
+#pragma unroll
+                    for (int c = 0; c < W2 / 2; ++c) acc[k][c] = fma2(rw, z2[c], acc[k][c]);
+                }
+            }
+            __syncwarp();
+            if (newpiece) {
+                // the two half-warps hold the same rows: fold the upper half into the lower,
+                // which adds the cell's footprint into the warp's tile
+                int lc[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k)
+#pragma unroll
+                    for (int c = 0; c < W2 / 2; ++c) {
+                        f32x2 o;
+                        o.x = __shfl_down_sync(0xffffffffu, acc[k][c].x, 16);
+                        o.y = __shfl_down_sync(0xffffffffu, acc[k][c].y, 16);
+                        acc[k][c] = add2(acc[k][c], o);
+                    }
+                if (half == 0) {
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int ra = g + S * k;
+                        float *dst = tile + ((lc[0] + ra) * TW + (lc[1] + rb)) * TW + lc[2];
+#pragma unroll
+                        for (int c = 0; c < W2 / 2; ++c) {
+                            dst[2 * c] += acc[k][c].x;
+                            dst[2 * c + 1] += acc[k][c].y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < RPL; ++k)
+#pragma unroll
+                    for (int c = 0; c < W2 / 2; ++c) acc[k][c] = zero2();
+                __syncwarp();
+            }
+            if (done) break;
+            s = sn;
+            q = qn;
+            send = sendn;
+            if (newpiece) {
+                sg = sgn;
+                sg_next = sg_next2;
+            }
+            cnt = cntn;
+            fx = nfx;
+            fy = nfy;
+            fz = nfz;
+            vv = nvv;
+        }
+    }
+    __syncthreads();
+    float *out = reinterpret_cast<float *>(a.tiles) + ((size_t)wi_idx * a.nrhs + r) * C::TV;
+    for (int i = threadIdx.x; i < C::TV; i += NWARP * 32) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NWARP; ++w) s2 += tiles_s[w * C::TVP + i];
+        out[i] = s2;
+    }
+}
+
+// v in sorted order (one copy per window), so that the spread reads it coalesced
+template <typename T>
+__global__ void k_gather_v(const T *__restrict__ v, const int *__restrict__ perm, long long n,
+                           long long total, long long q0, long long q1, int nrhs, T *__restrict__ vs) {
+    const long long cnt = q1 - q0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt * nrhs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / cnt, q = q0 + (t - r * cnt);
+        vs[r * total + q] = v[r * n + perm[q]];
+    }
+}
+
 // ------------------------------------------------------------------ work-item tiles -> bin tile
 // A bin split into several work items has several partial tiles; they are summed, in work-item
 // order, into the slot of the bin's first work item, so the grid gather reads one tile per bin.
@@ -174,28 +400,36 @@ struct BinReduceArgs {
     void *tiles;
     const int4 *mbins;           // {first work item, count, tile volume, 0} of multi-item bins
     int nmbins, nrhs, mb_begin;
+    int tv_max;                  // largest tile volume among these bins (sets the chunk count)
 };
+
+// One CTA per (bin, chunk of 32 tile elements): warp k sums the work items k, k+8, k+16, ...
+// of its 32 elements, then warp 0 adds the eight partial sums in a fixed order.
+constexpr int kBinReduceChunk = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bin_reduce(BinReduceArgs a) {
-    const int b = a.mb_begin + blockIdx.x;
+    __shared__ T part[8][kBinReduceChunk];
+    const int chunks = (a.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
+    const int b = a.mb_begin + blockIdx.x / chunks;
+    const int c = blockIdx.x % chunks;
     const int r = blockIdx.y;
-    if (b >= a.mb_begin + a.nmbins) return;
     const int4 mb = a.mbins[b];
     const int tv = mb.z;
+    const int e = c * kBinReduceChunk + (threadIdx.x & 31);
+    const int slice = threadIdx.x >> 5;
+    if (c * kBinReduceChunk >= tv) return;  // whole CTA: this bin's tile is shorter
     T *tiles = reinterpret_cast<T *>(a.tiles);
-    for (int e = threadIdx.x; e < tv; e += blockDim.x) {
-        T acc[8];
+    T s = T(0);
+    if (e < tv)
+        for (int k = slice; k < mb.y; k += 8) s += tiles[((size_t)(mb.x + k) * a.nrhs + r) * tv + e];
+    part[slice][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (slice == 0 && e < tv) {
+        T t = part[0][threadIdx.x];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = T(0);
-        int k = 0;
-        for (; k + 8 <= mb.y; k += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] += tiles[((size_t)(mb.x + k + u) * a.nrhs + r) * tv + e];
-        }
-        for (int u = 0; k + u < mb.y; ++u) acc[u] += tiles[((size_t)(mb.x + k + u) * a.nrhs + r) * tv + e];
-        T s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-        tiles[((size_t)mb.x * a.nrhs + r) * tv + e] = s;
+        for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
+        tiles[((size_t)mb.x * a.nrhs + r) * tv + e] = t;
     }
 }
 
@@ -337,14 +571,35 @@ __global__ void __launch_bounds__(NWARP * 32) k_interp(InterpArgs a) {
             for (int aa = 0; aa < W2; ++aa) {
                 const T *plane = blk + aa * W2 * W2;
                 T sa = T(0);
+                if constexpr (sizeof(T) == 4 && W2 % 4 == 0) {
+                    // inner products along c on f32x2 pairs (two FMAs per instruction)
+                    f32x2 wz2[W2 / 2];
 #pragma unroll
-                for (int bb = 0; bb < W2; ++bb) {
-                    T row[W2];
-                    lds_vec<T, W2>(plane + bb * W2, row);
-                    T sb = T(0);
+                    for (int cc = 0; cc < W2 / 2; ++cc) wz2[cc] = pack2(wt[2][2 * cc], wt[2][2 * cc + 1]);
 #pragma unroll
-                    for (int cc = 0; cc < W2; ++cc) sb = fma(row[cc], wt[2][cc], sb);
-                    sa = fma(wt[1][bb], sb, sa);
+                    for (int bb = 0; bb < W2; ++bb) {
+                        f32x2 sb2 = zero2();
+#pragma unroll
+                        for (int cc = 0; cc < W2 / 2; cc += 2) {
+                            f32x2 t0, t1;
+                            lds_pairs(plane + bb * W2 + 2 * cc, t0, t1);
+                            sb2 = fma2(t0, wz2[cc], sb2);
+                            sb2 = fma2(t1, wz2[cc + 1], sb2);
+                        }
+                        float lo, hi;
+                        unpack2(sb2, lo, hi);
+                        sa = fma(wt[1][bb], lo + hi, sa);
+                    }
+                } else {
+#pragma unroll
+                    for (int bb = 0; bb < W2; ++bb) {
+                        T row[W2];
+                        lds_vec<T, W2>(plane + bb * W2, row);
+                        T sb = T(0);
+#pragma unroll
+                        for (int cc = 0; cc < W2; ++cc) sb = fma(row[cc], wt[2][cc], sb);
+                        sa = fma(wt[1][bb], sb, sa);
+                    }
                 }
                 f = fma(wx[0], sa, f);
 #pragma unroll
@@ -365,6 +620,129 @@ __global__ void __launch_bounds__(NWARP * 32) k_interp(InterpArgs a) {
             for (int cc = 0; cc < W2; ++cc) f = fma(blk[cc], wt[0][cc], f);
         }
         if (valid) out[a.perm[q]] = f;
+    }
+}
+
+// ------------------------------------------------------------------ FP32 3-D interpolation
+// One CTA per spread work item (one bin's run of cells). The bin's grid neighbourhood is staged in
+// shared memory as B shifted copies: copy s holds, for every (x, y) of the neighbourhood, the 2M
+// values along the last axis that a cell with last local coordinate s needs, 16-byte aligned.
+// Any lane can then read its own cell's rows with 128-bit loads, so a warp evaluates 32
+// consecutive points per batch (one per lane) whatever cells they fall in; lanes of one cell
+// share addresses (broadcast). Per-point inputs of the next batch load while the current batch
+// computes; inner products along the last axis use f32x2 pairs.
+struct InterpWiArgs {
+    const int4 *wis;
+    const int4 *segs;
+    const float *frac;
+    const int *perm;
+    const unsigned char *cellloc;  // cell index inside its bin, (l0 B + l1) B + l2, per sorted point
+    const float *grid;       // [nrhs][grid_total]
+    const DevWindow *dwin;
+    float *part;             // [P][nrhs][n] by internal window (offset by part_w0)
+    long long n, total, grid_stride_rhs;
+    int nrhs, wi_begin, wi_end, n_os, part_w0;
+    WinParams wp;
+};
+
+template <int M, int B, int NWARP>
+struct InterpX2Cfg {
+    static constexpr int W2 = 2 * M;
+    static constexpr int TW = B + W2 - 1;
+    static constexpr int ROWS = TW * TW;
+    static constexpr size_t smem = sizeof(float) * (size_t)B * ROWS * W2;
+};
+
+template <int M, int B, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32) k_interp3_x2(InterpWiArgs a) {
+    using C = InterpX2Cfg<M, B, NWARP>;
+    constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS;
+    static_assert(W2 % 4 == 0, "pairs along the last axis");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *cp = reinterpret_cast<float *>(smem_raw);
+
+    const int wi_idx = a.wi_begin + blockIdx.x;
+    if (wi_idx >= a.wi_end) return;
+    const int r = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 wi = a.wis[wi_idx];
+    const int w = wi.x;
+    const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
+    const DevWindow dw = a.dwin[w];
+    const float *grid = a.grid + (size_t)r * a.grid_stride_rhs + dw.grid_off;
+    {
+        const int o0 = bin[0] * B - M + 1, o1 = bin[1] * B - M + 1, o2 = bin[2] * B - M + 1;
+        for (int e = threadIdx.x; e < B * ROWS * W2; e += NWARP * 32) {
+            const int c = e % W2, row = (e / W2) % ROWS, sh = e / (W2 * ROWS);
+            const int x = row / TW, y = row % TW;
+            cp[e] = grid[((long long)(o0 + x) * a.n_os + (o1 + y)) * a.n_os + (o2 + sh + c)];
+        }
+    }
+    __syncthreads();
+    const int4 s_first = a.segs[wi.y];
+    const int4 s_last = a.segs[wi.z - 1];
+    const int p0 = s_first.y, p1 = s_last.y + s_last.z;
+    const int len = p1 - p0;
+    const int pw0 = p0 + (int)(((long long)len * warp) / NWARP);
+    const int pw1 = p0 + (int)(((long long)len * (warp + 1)) / NWARP);
+    if (pw0 >= pw1) return;
+    const float *fr0 = a.frac, *fr1 = a.frac + a.total, *fr2 = a.frac + 2 * a.total;
+    float *out = a.part + ((size_t)(w - a.part_w0) * a.nrhs + r) * a.n;
+
+    // current batch inputs (lanes past the range keep a valid point's data and do not write)
+    int q = pw0 + min(lane, pw1 - pw0 - 1);
+    float fx = fr0[q], fy = fr1[q], fz = fr2[q];
+    int pi = a.perm[q];
+    int loc = a.cellloc[q];
+    for (int qb = pw0; qb < pw1; qb += 32) {
+        const bool valid = qb + lane < pw1;
+        const int qbn = qb + 32;
+        float nfx = fx, nfy = fy, nfz = fz;
+        int npi = pi, nloc = loc;
+        if (qbn < pw1) {
+            const int qn = qbn + min(lane, pw1 - qbn - 1);
+            nfx = fr0[qn];
+            nfy = fr1[qn];
+            nfz = fr2[qn];
+            npi = a.perm[qn];
+            nloc = a.cellloc[qn];
+        }
+        float wx[W2], wy[W2], wz[W2];
+        Weights<float, M>::eval(fx, a.wp, wx);
+        Weights<float, M>::eval(fy, a.wp, wy);
+        Weights<float, M>::eval(fz, a.wp, wz);
+        f32x2 wz2[W2 / 2];
+#pragma unroll
+        for (int cc = 0; cc < W2 / 2; ++cc) wz2[cc] = make_float2(wz[2 * cc], wz[2 * cc + 1]);
+        const int l2 = loc % B, l1 = (loc / B) % B, l0 = loc / (B * B);
+        const float *base = cp + ((size_t)l2 * ROWS + l0 * TW + l1) * W2;
+        float f = 0.0f;
+#pragma unroll 1
+        for (int aa = 0; aa < W2; ++aa) {
+            const float *plane = base + aa * TW * W2;
+            float sa = 0.0f;
+#pragma unroll
+            for (int bb = 0; bb < W2; ++bb) {
+                f32x2 sb2 = zero2();
+#pragma unroll
+                for (int cc = 0; cc < W2 / 2; cc += 2) {
+                    f32x2 t0, t1;
+                    lds_pairs(plane + bb * W2 + 2 * cc, t0, t1);
+                    sb2 = fma2(t0, wz2[cc], sb2);
+                    sb2 = fma2(t1, wz2[cc + 1], sb2);
+                }
+                sa = fmaf(wy[bb], sb2.x + sb2.y, sa);
+            }
+            f = fmaf(wx[0], sa, f);
+#pragma unroll
+            for (int k = 0; k < W2 - 1; ++k) wx[k] = wx[k + 1];
+        }
+        if (valid) out[pi] = f;
+        fx = nfx;
+        fy = nfy;
+        fz = nfz;
+        pi = npi;
+        loc = nloc;
     }
 }
 

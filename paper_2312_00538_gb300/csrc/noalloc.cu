@@ -50,6 +50,7 @@ anova_status spread_noalloc(anova_plan *p, int w, const void *v, void *grid) {
     cudaStream_t s = p->stream;
 
     SpreadArgs sa;
+    sa.vsorted = nullptr;  // generic spread: no sorted copy of v (that would need workspace)
     sa.wis = p->wis;
     sa.segs = p->segs;
     sa.frac = p->frac;
@@ -77,8 +78,10 @@ anova_status spread_noalloc(anova_plan *p, int w, const void *v, void *grid) {
     ba.mb_begin = wi.mb_begin;
     ba.nmbins = wi.mb_end - wi.mb_begin;
     ba.nrhs = 1;
+    ba.tv_max = (int)tv;
     if (ba.nmbins > 0) {
-        k_bin_reduce<T><<<dim3(ba.nmbins, 1), 256, 0, s>>>(ba);
+        const int chunks = (ba.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
+        k_bin_reduce<T><<<dim3(ba.nmbins * chunks, 1), 256, 0, s>>>(ba);
         ANOVA_CUDA_TRY(cudaGetLastError());
     }
     ReduceArgs ra;

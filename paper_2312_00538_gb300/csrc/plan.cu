@@ -134,6 +134,20 @@ __global__ void k_gather(const uint32_t *__restrict__ keys, const int *__restric
     }
 }
 
+// FP64 window coordinates in original point order, structure of arrays (window, feature, point)
+__global__ void k_window_coords(const double *__restrict__ X, long long n, int d,
+                                const int *__restrict__ feat, const int *__restrict__ dws, int P,
+                                double *__restrict__ xw) {
+    const long long total = n * P;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(q / n);
+        const long long i = q - (long long)w * n;
+        for (int k = 0; k < 3; ++k)
+            xw[((long long)w * 3 + k) * n + i] = k < dws[w] ? X[i * d + feat[3 * w + k]] : 0.0;
+    }
+}
+
 int ilog2(int x) {
     int l = 0;
     while ((1 << l) < x) ++l;
@@ -167,7 +181,8 @@ void release_workspace(anova_plan *p) {
     if (p->grids) cudaFree(p->grids);
     if (p->tiles) cudaFree(p->tiles);
     if (p->part) cudaFree(p->part);
-    p->grids = p->tiles = p->part = nullptr;
+    if (p->vsorted) cudaFree(p->vsorted);
+    p->grids = p->tiles = p->part = p->vsorted = nullptr;
     p->ws_rhs = 0;
     p->ws_bytes = 0;
 }
@@ -184,16 +199,18 @@ anova_status ensure_workspace(anova_plan *p, int nrhs) {
     const size_t gbytes = es * 4 * (size_t)nrhs * p->grid_total;
     const size_t tbytes = es * std::max<size_t>(1, (size_t)p->nwi * nrhs * tv);
     const size_t pbytes = es * (size_t)p->P * nrhs * p->n;
+    const size_t vbytes = p->prec == ANOVA_FP32 ? sizeof(float) * (size_t)p->P * nrhs * p->n : 16;
     if ((e = cudaMalloc(&p->grids, gbytes)) != cudaSuccess ||
         (e = cudaMalloc(&p->tiles, tbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&p->part, pbytes)) != cudaSuccess) {
+        (e = cudaMalloc(&p->part, pbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&p->vsorted, vbytes)) != cudaSuccess) {
         release_workspace(p);
         return fail(ANOVA_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
     }
     e = cudaMemsetAsync(p->grids, 0, gbytes, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     p->ws_rhs = nrhs;
-    p->ws_bytes = (int64_t)(gbytes + tbytes + pbytes);
+    p->ws_bytes = (int64_t)(gbytes + tbytes + pbytes + vbytes);
     return ANOVA_OK;
 }
 
@@ -201,7 +218,7 @@ void destroy_plan(anova_plan *p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->perm, p->segs, p->wis, p->bins, p->mbins, p->ftiles, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->bins, p->mbins, p->ftiles, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -368,6 +385,13 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
         else
             k_gather<float><<<nb, 256, 0, st>>>(kin, vin, (const double *)dX.p, n, d, (const int *)dfeat.p,
                                                 (const int *)ddws.p, P, nos, KB, (float *)p->frac, p->perm);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+    }
+    ANOVA_CUDA_TRY(cudaMalloc(&p->xw, sizeof(double) * 3 * total));
+    {
+        const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+        k_window_coords<<<nb, 256, 0, st>>>((const double *)dX.p, n, d, (const int *)dfeat.p,
+                                            (const int *)ddws.p, P, p->xw);
         ANOVA_CUDA_TRY(cudaGetLastError());
     }
     std::vector<uint32_t> hkeys(total);
@@ -596,6 +620,18 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     if ((s = upload((void **)&p->wis, wis.data(), sizeof(int4) * wis.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->bins, bins.data(), sizeof(int2) * bins.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->mbins, mbins.data(), sizeof(int4) * mbins.size())) != ANOVA_OK) return s;
+    {
+        // cell index inside its bin for every sorted point (the low digits of the sort key)
+        std::vector<unsigned char> loc(total);
+        for (long long q = 0; q < total; ++q) {
+            const int w = (int)(hkeys[q] >> KB);
+            uint32_t bvol = 1;
+            for (int k = 0; k < p->win[w].dw; ++k) bvol *= (uint32_t)B;
+            loc[q] = (unsigned char)((hkeys[q] & kmask) % bvol);
+        }
+        if ((s = upload((void **)&p->cellloc, loc.data(), loc.size())) != ANOVA_OK) return s;
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
     std::vector<float> f32;
@@ -611,7 +647,7 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
         if ((s = upload(&p->tw, f32.data(), sizeof(float) * f32.size())) != ANOVA_OK) return s;
         ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    p->static_bytes += (int64_t)(es * 3 * total + sizeof(int) * total);
+    p->static_bytes += (int64_t)(es * 3 * total + sizeof(int) * total + sizeof(double) * 3 * total);
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     *out = plan.release();
     return ANOVA_OK;

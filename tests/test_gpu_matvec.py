@@ -242,3 +242,20 @@ def test_config2_sixteen_rhs_sampled_rows(env):
     ref = ok.anova_matvec(X, W, 1.0, V, rows=idx)
     for r in range(16):
         assert rel_l2(got[idx, r], ref[:, r]) <= FP32_BAR
+
+
+@pytest.mark.parametrize("prec,m", [("fp32", 2), ("fp32", 3), ("fp32", 5), ("fp32", 6),
+                                    ("fp64", 3), ("fp64", 4), ("fp64", 5)])
+def test_other_window_cutoffs_match_plain_nfft(env, prec, m):
+    """Every compiled cut-off m against the oracle's plain NFFT with the same N and m."""
+    torch, ab = env
+    rng = np.random.default_rng(100 + m)
+    X = minmax_scale(rng.standard_normal((400, 6)))
+    W = np.array([[0, 1, 2], [3, 4, -1], [5, -1, -1]])
+    v = rng.standard_normal(400)
+    fl = ab.ANOVA_FP64 if prec == "fp64" else ab.ANOVA_FP32
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = ab.anova_nfft_plan(X, W, 0.6, N=16, m=m, flags=fl)
+    got = _run(torch, ab, plan, v, dt)
+    ref = on.nfft_fastsum(X, W, 0.6, 16, m, v)
+    assert rel_l2(got, ref) <= (1e-12 if prec == "fp64" else 3e-6)
