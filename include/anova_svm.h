@@ -1,0 +1,126 @@
+/*
+ * anova_svm.h -- low-rank preconditioners and the SVM interior point method of arXiv 2312.00538
+ * (Wagner, Pearson, Stoll) on top of the ANOVA-NFFT matvec of anova.h.
+ *
+ * The dual soft-margin SVM (Sec. 1, eq. (kernelsvm)): max_alpha e^T alpha - 1/2 alpha^T Y K Y alpha
+ * subject to 0 <= alpha_i <= C, y^T alpha = 0, with the ANOVA kernel K of anova.h. The interior
+ * point method is Algorithm 1 (Sec. 2); every Newton system (Sec. 2, eq. (Newton))
+ *     [[Y K Y + Theta, -y], [-y^T, 0]] [d_alpha; d_lambda] = rhs
+ * is solved by preconditioned MINRES (Secs. 3, 5) whose operator uses the FP32 plan, inside
+ * iterative refinement against residuals computed with the FP64 plan. The preconditioner is
+ * blockdiag(A^, y^T A^{-1} y) with A^ = Theta + Y L L^T Y from a low-rank factor K ~ L L^T
+ * (Sec. 4: pivoted Cholesky, Algorithm 2, or Nystrom) applied by the Woodbury identity (Sec. 5).
+ *
+ * Conventions as in anova.h: status returns, thread-local anova_last_error(), caller-owned
+ * buffers, work on the plan's stream.
+ */
+#ifndef ANOVA_SVM_H
+#define ANOVA_SVM_H
+
+#include "anova.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * lowrank_precond_build -- low-rank factor K ~ L L^T (L: n x rank, rank <= r) of the plan's
+ * kernel K = sum_l K_l, with the kernel entries evaluated exactly (FP64) from the plan's
+ * coordinates.
+ *   kind = PCHOL_GREEDY: Algorithm 2 (greedy pivoted Cholesky), pivot = arg-max of the residual
+ *          diagonal, ties to the lowest index; stops at rank r or when the largest residual
+ *          diagonal is <= err_tol * max(diag K) (Table 1: err_tol = 1e-5).
+ *   kind = NYSTROM: K(:,S) K(S,S)^{-1} K(S,:) on the pivot set S of the greedy pass, with the
+ *          core K(S,S) factored as L D L^T and entries of D below 1e-10 max D set to that value
+ *          (Sec. 4).
+ * seed is reserved for randomised variants and ignored by these two kinds.
+ * The plan must outlive the preconditioner. Requires eta_l >= 0 (K positive semidefinite).
+ * Errors: INVALID_ARG (r outside [1, 1024], bad kind, negative eta), OOM, CUDA.
+ */
+anova_status lowrank_precond_build(anova_plan_t plan, int kind, int r, double err_tol,
+                                   uint64_t seed, lowrank_t *out);
+
+/* Rank reached and (optionally, host, rank entries) the pivots in the order they were chosen. */
+anova_status lowrank_info(lowrank_t lr, int *rank, int64_t *pivots);
+
+/* Copy the FP64 factor L (n x rank, column-major) to the device buffer L. Synchronous. */
+anova_status lowrank_factor(lowrank_t lr, double *L);
+
+/*
+ * lowrank_precond_set_theta -- prepare the Woodbury core for one interior point step:
+ * M = I + L^T Theta^{-1} L (FP64 accumulation from an FP32 copy of L), its Cholesky factor,
+ * and the Schur value s = y^T A^{-1} y. theta, y: device, n doubles; theta > 0, y in {-1, +1}.
+ * Errors: BREAKDOWN if M or s is not positive. Synchronises the stream.
+ */
+anova_status lowrank_precond_set_theta(lowrank_t lr, const double *theta, const double *y);
+
+/*
+ * lowrank_precond_apply -- x = blockdiag(A^, s)^{-1} g for the saddle system of size n + 1:
+ * x[0:n] = A^{-1} g[0:n] by the Woodbury identity (Sec. 5), x[n] = g[n] / s. theta and y must be
+ * the arrays given to the last lowrank_precond_set_theta. g, x: device, n + 1 doubles, distinct.
+ */
+anova_status lowrank_precond_apply(lowrank_t lr, const double *theta, const double *y,
+                                   const double *g, double *x);
+
+void lowrank_destroy(lowrank_t lr);
+
+/* Stopping rules of the interior point loop. */
+enum {
+    SVM_STOP_GAP = 0,  /* relative duality gap and |y^T alpha| below tol (default) */
+    SVM_STOP_ALG1 = 1  /* Algorithm 1's test: mu and both relative infeasibilities below tol */
+};
+
+typedef struct {
+    int max_iter;            /* interior point iterations (Table 1: 50) */
+    double sigma_barrier;    /* barrier reduction mu <- sigma mu (Table 1: 0.6) */
+    double gamma;            /* step factor to the boundary (Table 1: 0.99995) */
+    int stop;                /* SVM_STOP_GAP or SVM_STOP_ALG1 */
+    int krylov_max;          /* MINRES iterations per solve (Table 1: 100) */
+    double krylov_tol;       /* relative residual of each Newton solve (default 1e-8) */
+    int refine_max;          /* FP64 refinement passes per Newton solve (default 4) */
+    int precond;             /* PCHOL_GREEDY or NYSTROM */
+    int rank;                /* preconditioner rank (default 200, at most n) */
+    double err_tol;          /* pivoted-Cholesky tolerance (Table 1: 1e-5) */
+    uint64_t seed;
+    double ell;              /* kernel length scale (default 1) */
+    const int32_t *windows;  /* P x 3 windows (-1 padded); NULL: consecutive 3-feature windows */
+    int P;
+    int N, m;                /* FP32 plan (default 32, 4) */
+    int N_precise, m_precise;/* FP64 plan for residuals and objectives (default 64, 6) */
+    int scale_features;      /* 1: min-max scale every feature into [-0.2, 0.2] first */
+    void *cuda_stream;
+} svm_opts;
+
+typedef struct {
+    int iterations;          /* interior point iterations done */
+    int krylov_iterations;   /* MINRES iterations over all Newton solves */
+    int refinements;         /* refinement passes over all Newton solves */
+    int rank;                /* preconditioner rank */
+    int converged;           /* 1 if the stopping rule was met */
+    double mu;               /* final barrier parameter */
+    double dual;             /* e^T alpha - 1/2 alpha^T Y K Y alpha (FP64 plan) */
+    double primal;           /* 1/2 alpha^T Y K Y alpha + C sum hinge(1 - y_i (f_i + b)) */
+    double rel_gap;          /* (primal - dual) / max(1, |primal|) */
+    double xi_alpha;         /* |y^T alpha| / max(1, |y^T alpha^0|) */
+    double time_ms;          /* wall time of the solve */
+} svm_stats;
+
+/* Table 1 defaults and the readings documented with the library. */
+void svm_opts_default(svm_opts *opts);
+
+/*
+ * svm_ipm_solve -- train the soft-margin kernel SVM by Algorithm 1.
+ * X: host, n x d row-major FP64 points (in [-0.2, 0.2] unless opts->scale_features);
+ * y: host, n labels in {-1, +1}; C > 0; tol > 0 (stopping tolerance of opts->stop).
+ * alpha: host, n doubles (output); b: host, the bias b = -lambda (output); stats nullable.
+ * Returns NOT_CONVERGED (with the last iterate in alpha, b) if max_iter is reached first.
+ */
+anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *y, double C,
+                           double tol, const svm_opts *opts, double *alpha, double *b,
+                           svm_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANOVA_SVM_H */

@@ -67,6 +67,14 @@ _SIGNATURES = {
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
     "anova_kernel_coeffs": (_c_int, [_c_dbl, _c_int, _dp]),
     "anova_window_hat": (_c_int, [_c_int, _c_int, _c_int, _dp]),
+    "lowrank_precond_build": (_c_int, [_vp, _c_int, _c_int, _c_dbl, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "lowrank_info": (_c_int, [_vp, ctypes.POINTER(_c_int), _lp]),
+    "lowrank_factor": (_c_int, [_vp, _vp]),
+    "lowrank_precond_set_theta": (_c_int, [_vp, _vp, _vp]),
+    "lowrank_precond_apply": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lowrank_destroy": (None, [_vp]),
+    "svm_opts_default": (None, [_vp]),
+    "svm_ipm_solve": (_c_int, [_dp, _c_i64, _c_int, _dp, _c_dbl, _c_dbl, _vp, _dp, _dp, _vp]),
     "anova_last_error": (ctypes.c_char_p, []),
     "anova_version": (ctypes.c_char_p, []),
 }
@@ -274,3 +282,114 @@ def anova_last_error():
 
 def anova_version():
     return lib().anova_version().decode()
+
+
+# --------------------------------------------------------------------------- solver (anova_svm.h)
+SVM_STOP_GAP = 0
+SVM_STOP_ALG1 = 1
+
+
+class svm_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("sigma_barrier", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("stop", ctypes.c_int), ("krylov_max", ctypes.c_int),
+                ("krylov_tol", ctypes.c_double), ("refine_max", ctypes.c_int),
+                ("precond", ctypes.c_int), ("rank", ctypes.c_int), ("err_tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("ell", ctypes.c_double),
+                ("windows", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int),
+                ("N", ctypes.c_int), ("m", ctypes.c_int), ("N_precise", ctypes.c_int),
+                ("m_precise", ctypes.c_int), ("scale_features", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class svm_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rank", ctypes.c_int), ("converged", ctypes.c_int),
+                ("mu", ctypes.c_double), ("dual", ctypes.c_double), ("primal", ctypes.c_double),
+                ("rel_gap", ctypes.c_double), ("xi_alpha", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class LowRank:
+    """Owns a lowrank_t (and keeps its plan alive)."""
+
+    def __init__(self, handle, plan):
+        self.handle = handle
+        self.plan = plan
+
+    def destroy(self):
+        if self.handle:
+            lib().lowrank_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def lowrank_precond_build(plan, kind=PCHOL_GREEDY, r=200, err_tol=1e-5, seed=0):
+    h = _vp()
+    _check(lib().lowrank_precond_build(plan.handle, int(kind), int(r), float(err_tol),
+                                       ctypes.c_uint64(seed), ctypes.byref(h)))
+    return LowRank(h, plan)
+
+
+def lowrank_info(lr):
+    rank = ctypes.c_int()
+    _check(lib().lowrank_info(lr.handle, ctypes.byref(rank), None))
+    piv = np.zeros(rank.value, dtype=np.int64)
+    _check(lib().lowrank_info(lr.handle, ctypes.byref(rank), _ptr(piv, ctypes.c_int64)))
+    return rank.value, piv
+
+
+def lowrank_factor(lr, L):
+    """Copies the FP64 factor into the device tensor L (n x rank, column-major: shape (rank, n))."""
+    _check(lib().lowrank_factor(lr.handle, _dev_ptr(L)))
+
+
+def lowrank_precond_set_theta(lr, theta, y):
+    _check(lib().lowrank_precond_set_theta(lr.handle, _dev_ptr(theta), _dev_ptr(y)))
+
+
+def lowrank_precond_apply(lr, theta, y, g, x):
+    _check(lib().lowrank_precond_apply(lr.handle, _dev_ptr(theta), _dev_ptr(y), _dev_ptr(g),
+                                       _dev_ptr(x)))
+
+
+def lowrank_destroy(lr):
+    lr.destroy()
+
+
+def svm_opts_default():
+    o = svm_opts()
+    lib().svm_opts_default(ctypes.byref(o))
+    return o
+
+
+def svm_ipm_solve(X, y, C, tol, opts=None, windows=None):
+    """svm_ipm_solve: host X (n x d) and labels y; returns (alpha, b, stats dict, status).
+
+    Raises AnovaError except for ANOVA_ERR_NOT_CONVERGED, which is returned as the status."""
+    X = _f64(X)
+    yv = _f64(y)
+    n, d = X.shape
+    o = opts if opts is not None else svm_opts_default()
+    keep = None
+    if windows is not None:
+        keep = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 3)
+        o.windows = _ptr(keep, ctypes.c_int32)
+        o.P = keep.shape[0]
+    alpha = np.zeros(n)
+    b = ctypes.c_double()
+    st = svm_stats()
+    status = lib().svm_ipm_solve(_ptr(X, ctypes.c_double), n, d, _ptr(yv, ctypes.c_double),
+                                 float(C), float(tol), ctypes.byref(o),
+                                 _ptr(alpha, ctypes.c_double), ctypes.byref(b), ctypes.byref(st))
+    if status not in (ANOVA_OK, ANOVA_ERR_NOT_CONVERGED):
+        _check(status)
+    del keep
+    return alpha, b.value, st.as_dict(), status

@@ -43,7 +43,7 @@ def build(force=False, verbose=False, extra=()):
     """Compile and link libanova.so; returns its path. Skips work when it is up to date."""
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(f) <= t for f in _deps() + [os.path.join(HERE, "..", "include", "anova.h")]):
+        if all(os.path.getmtime(f) <= t for f in _deps() + glob.glob(os.path.join(HERE, "..", "include", "*.h"))):
             return LIB
     os.makedirs(OBJ, exist_ok=True)
     srcs = _sources()

@@ -1,0 +1,580 @@
+// Interior point method for the kernel SVM dual (arXiv 2312.00538, Sec. 2, Algorithm 1) with
+// Newton systems (eq. (Newton)) solved by preconditioned MINRES (Secs. 3, 5) on the FP32
+// ANOVA-NFFT operator, refined against FP64-plan residuals. Vectors live on the device in FP64;
+// the host runs the scalar recurrences (dot products come back as per-block partial sums that
+// the host adds in a fixed order, so results are reproducible). Also exports the low-rank
+// preconditioner calls of anova_svm.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/anova_svm.h"
+#include "anova_internal.h"
+#include "lowrank_internal.h"
+
+namespace anova {
+anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                         const double *ell, const double *eta, int N, int m, int flags,
+                         void *stream, anova_plan_t *out);
+void destroy_plan(anova_plan *p);
+
+namespace {
+
+constexpr int kRedBlocks = 256;
+
+__global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, long long n,
+                      double *__restrict__ part) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// out = scale * sum(part[0..np)) written on the device (no host round trip)
+__global__ void k_sum_to(const double *__restrict__ part, int np, double scale, double *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += part[i];
+        *out = scale * s;
+    }
+}
+
+__global__ void k_yx_f32(const double *__restrict__ x, const double *__restrict__ y, long long n, float *__restrict__ t) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        t[i] = (float)(y[i] * x[i]);
+}
+
+__global__ void k_yx_f64(const double *__restrict__ x, const double *__restrict__ y, long long n, double *__restrict__ t) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        t[i] = y[i] * x[i];
+}
+
+// out[i] = y_i (K t)_i + theta_i x_i - y_i x_n   (the (1,1) and (1,2) blocks of eq. (Newton))
+template <typename K>
+__global__ void k_saddle_post(const K *__restrict__ Kt, const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ theta, long long n, double *__restrict__ out) {
+    const double xn = x[n];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = y[i] * (double)Kt[i] + theta[i] * x[i] - y[i] * xn;
+}
+
+__global__ void k_scale(const double *__restrict__ a, double s, long long n, double *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = s * a[i];
+}
+
+// out = a + sb * b + sc * c
+__global__ void k_lin3(const double *__restrict__ a, const double *__restrict__ b, const double *__restrict__ c,
+                       double sb, double sc, long long n, double *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] + sb * b[i] + sc * c[i];
+}
+
+// w_new = (v - eps w2 - delta w1) / gamma (into w2's buffer); x += phi w_new
+__global__ void k_minres_w(const double *__restrict__ v, double *__restrict__ w2, const double *__restrict__ w1,
+                           double eps, double delta, double inv_gamma, double phi, long long n, double *__restrict__ x) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double w = (v[i] - eps * w2[i] - delta * w1[i]) * inv_gamma;
+        w2[i] = w;
+        x[i] += phi * w;
+    }
+}
+
+__global__ void k_axpy(double a, const double *__restrict__ x, long long n, double *__restrict__ y) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+__global__ void k_sub(const double *__restrict__ a, const double *__restrict__ b, long long n, double *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void k_fill_d(double *x, long long n, double v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// Theta = mu (1/alpha^2 + 1/(C - alpha)^2) (Sec. 2)
+__global__ void k_theta(const double *__restrict__ al, double mu, double C, long long n, double *__restrict__ th) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = al[i], c = C - a;
+        th[i] = mu * (1.0 / (a * a) + 1.0 / (c * c));
+    }
+}
+
+// rhs_i = 1 - y_i f_i + lambda y_i + mu/alpha_i - mu/(C - alpha_i), f = K (y .* alpha) (eq. (Newton))
+__global__ void k_newton_rhs(const double *__restrict__ al, const double *__restrict__ y, const double *__restrict__ f,
+                             double lam, double mu, double C, long long n, double *__restrict__ rhs) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = al[i];
+        rhs[i] = 1.0 - y[i] * f[i] + lam * y[i] + mu / a - mu / (C - a);
+    }
+}
+
+// per-block minimum of the step that keeps 0 <= alpha + s d <= C
+__global__ void k_step_partial(const double *__restrict__ al, const double *__restrict__ d, double C, long long n,
+                               double *__restrict__ part) {
+    __shared__ double ws[32];
+    double s = INFINITY;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double di = d[i];
+        if (di < 0.0) s = fmin(s, -al[i] / di);
+        else if (di > 0.0) s = fmin(s, (C - al[i]) / di);
+    }
+    for (int o = 16; o > 0; o >>= 1) s = fmin(s, __shfl_down_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) s = fmin(s, __shfl_down_sync(0xffffffffu, s, o));
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// sums for the objectives: [0] sum alpha, [1] (y.*alpha)^T f, [2] sum hinge(1 - y (f + b)),
+// [3] y^T alpha, [4] ||xi_lambda||^2 with the current mu
+__global__ void k_objective_partial(const double *__restrict__ al, const double *__restrict__ y,
+                                    const double *__restrict__ f, double b, double lam, double mu, double C,
+                                    long long n, double *__restrict__ part) {
+    __shared__ double ws[5][32];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = al[i], yi = y[i], fi = f[i];
+        s[0] += a;
+        s[1] += yi * a * fi;
+        s[2] += fmax(0.0, 1.0 - yi * (fi + b));
+        s[3] += yi * a;
+        const double xl = 1.0 - yi * fi + lam * yi + mu / a - mu / (C - a);
+        s[4] += xl * xl;
+    }
+    for (int k = 0; k < 5; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) ws[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        for (int k = 0; k < 5; ++k) {
+            double v = threadIdx.x < (blockDim.x >> 5) ? ws[k][threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = v;
+        }
+    }
+}
+
+int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, kRedBlocks)); }
+
+// ------------------------------------------------------------------ solver state
+struct Solver {
+    anova_plan *p32 = nullptr, *p64 = nullptr;
+    lowrank *lr = nullptr;
+    cudaStream_t st = nullptr;
+    long long n = 0;
+    const double *y = nullptr, *theta = nullptr;  // device
+    double *part = nullptr;                      // kRedBlocks * 5 partials
+    std::vector<double> hpart;
+    float *t32 = nullptr, *k32 = nullptr;
+    double *t64 = nullptr, *k64 = nullptr;
+    int krylov_total = 0, refine_total = 0;
+
+    anova_status dot(const double *a, const double *b, long long len, double *out) {
+        const int nb = blocks_for(len);
+        k_dot<<<nb, 256, 0, st>>>(a, b, len, part);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        hpart.resize(nb);
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += hpart[i];
+        *out = s;
+        return ANOVA_OK;
+    }
+
+    // out = A x for the saddle matrix of eq. (Newton); precise selects the FP64 plan
+    anova_status apply(const double *x, double *out, bool precise) {
+        const int nb = blocks_for(n);
+        anova_status s;
+        if (precise) {
+            k_yx_f64<<<nb, 256, 0, st>>>(x, y, n, t64);
+            if ((s = run_matvec_t<double>(p64, t64, k64, 1, -1)) != ANOVA_OK) return s;
+            k_saddle_post<double><<<nb, 256, 0, st>>>(k64, x, y, theta, n, out);
+        } else {
+            k_yx_f32<<<nb, 256, 0, st>>>(x, y, n, t32);
+            if ((s = run_matvec_t<float>(p32, t32, k32, 1, -1)) != ANOVA_OK) return s;
+            k_saddle_post<float><<<nb, 256, 0, st>>>(k32, x, y, theta, n, out);
+        }
+        // out[n] = -y^T x[0:n]
+        k_dot<<<nb, 256, 0, st>>>(y, x, n, part);
+        k_sum_to<<<1, 32, 0, st>>>(part, nb, -1.0, out + n);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        return ANOVA_OK;
+    }
+
+    // K (y .* a) with the FP64 plan into f
+    anova_status kya(const double *a, double *f) {
+        const int nb = blocks_for(n);
+        k_yx_f64<<<nb, 256, 0, st>>>(a, y, n, t64);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        return run_matvec_t<double>(p64, t64, f, 1, -1);
+    }
+};
+
+// Preconditioned MINRES (Paige-Saunders) for A x = b, x0 = 0, vectors of length n + 1.
+anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxit, double *work[10], int *iters) {
+    const long long N1 = S.n + 1;
+    const int nb = blocks_for(N1);
+    double *r_prev = work[0], *r_cur = work[1], *r_next = work[2], *y_cur = work[3], *y_next = work[4];
+    double *v = work[5], *Av = work[6], *w1 = work[7], *w2 = work[8];
+    cudaStream_t st = S.st;
+    anova_status s;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N1, st));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(r_prev, 0, sizeof(double) * N1, st));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(w1, 0, sizeof(double) * N1, st));
+    ANOVA_CUDA_TRY(cudaMemsetAsync(w2, 0, sizeof(double) * N1, st));
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(r_cur, b, sizeof(double) * N1, cudaMemcpyDeviceToDevice, st));
+    if ((s = lowrank_apply_impl(S.lr, S.theta, S.y, r_cur, y_cur)) != ANOVA_OK) return s;
+    double beta1;
+    if ((s = S.dot(r_cur, y_cur, N1, &beta1)) != ANOVA_OK) return s;
+    *iters = 0;
+    if (beta1 < 0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: preconditioner is not positive definite");
+    beta1 = std::sqrt(beta1);
+    if (beta1 == 0.0) return ANOVA_OK;
+    double beta = beta1, beta_prev = 0.0, phibar = beta1;
+    double c_prev2 = 1.0, s_prev2 = 0.0, c_prev = 1.0, s_prev = 0.0;
+    for (int it = 1; it <= maxit; ++it) {
+        k_scale<<<nb, 256, 0, st>>>(y_cur, 1.0 / beta, N1, v);
+        if ((s = S.apply(v, Av, false)) != ANOVA_OK) return s;
+        double alpha;
+        if ((s = S.dot(v, Av, N1, &alpha)) != ANOVA_OK) return s;
+        k_lin3<<<nb, 256, 0, st>>>(Av, r_cur, r_prev, -alpha / beta, beta_prev > 0 ? -beta / beta_prev : 0.0, N1, r_next);
+        if ((s = lowrank_apply_impl(S.lr, S.theta, S.y, r_next, y_next)) != ANOVA_OK) return s;
+        double beta_next;
+        if ((s = S.dot(r_next, y_next, N1, &beta_next)) != ANOVA_OK) return s;
+        if (beta_next < 0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: preconditioner is not positive definite");
+        beta_next = std::sqrt(beta_next);
+        const double eps = s_prev2 * beta;
+        const double dbar = c_prev2 * beta;
+        const double delta = c_prev * dbar + s_prev * alpha;
+        const double gbar = -s_prev * dbar + c_prev * alpha;
+        double gamma = std::hypot(gbar, beta_next);
+        if (gamma == 0.0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: singular tridiagonal");
+        const double c = gbar / gamma, sn = beta_next / gamma;
+        const double phi = c * phibar;
+        phibar = -sn * phibar;
+        k_minres_w<<<nb, 256, 0, st>>>(v, w2, w1, eps, delta, 1.0 / gamma, phi, N1, x);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        std::swap(w1, w2);  // w1 <- newest w, w2 <- previous
+        c_prev2 = c_prev;
+        s_prev2 = s_prev;
+        c_prev = c;
+        s_prev = sn;
+        std::swap(r_prev, r_cur);
+        std::swap(r_cur, r_next);
+        std::swap(y_cur, y_next);
+        beta_prev = beta;
+        beta = beta_next;
+        *iters = it;
+        if (std::fabs(phibar) <= rtol * beta1 || beta == 0.0) break;
+    }
+    S.krylov_total += *iters;
+    return ANOVA_OK;
+}
+
+}  // namespace
+}  // namespace anova
+
+using namespace anova;
+
+extern "C" {
+
+anova_status lowrank_precond_build(anova_plan_t plan, int kind, int r, double err_tol, uint64_t seed,
+                                   lowrank_t *out) {
+    try {
+        return lowrank_build_impl(plan, kind, r, err_tol, seed, out);
+    } catch (...) {
+        return fail(ANOVA_ERR_OOM, "host allocation failed");
+    }
+}
+
+anova_status lowrank_info(lowrank_t lr, int *rank, int64_t *pivots) {
+    if (!lr) return fail(ANOVA_ERR_INVALID_ARG, "preconditioner is NULL");
+    if (rank) *rank = lr->rank;
+    if (pivots)
+        for (int i = 0; i < lr->rank; ++i) pivots[i] = lr->piv[i];
+    return ANOVA_OK;
+}
+
+anova_status lowrank_factor(lowrank_t lr, double *L) {
+    if (!lr || !L) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = lr->plan->stream;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(L, lr->L64, sizeof(double) * lr->n * lr->rank, cudaMemcpyDeviceToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    return ANOVA_OK;
+}
+
+anova_status lowrank_precond_set_theta(lowrank_t lr, const double *theta, const double *y) {
+    if (!lr || !theta || !y) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    return lowrank_set_theta_impl(lr, theta, y);
+}
+
+anova_status lowrank_precond_apply(lowrank_t lr, const double *theta, const double *y, const double *g, double *x) {
+    if (!lr || !theta || !y || !g || !x) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    if (g == x) return fail(ANOVA_ERR_INVALID_ARG, "g and x must be distinct");
+    return lowrank_apply_impl(lr, theta, y, g, x);
+}
+
+void lowrank_destroy(lowrank_t lr) {
+    if (!lr) return;
+    cudaStreamSynchronize(lr->plan->stream);
+    lowrank_release(lr);
+}
+
+void svm_opts_default(svm_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->max_iter = 50;
+    o->sigma_barrier = 0.6;
+    o->gamma = 0.99995;
+    o->stop = SVM_STOP_GAP;
+    o->krylov_max = 100;
+    o->krylov_tol = 1e-8;
+    o->refine_max = 4;
+    o->precond = PCHOL_GREEDY;
+    o->rank = 200;
+    o->err_tol = 1e-5;
+    o->seed = 0;
+    o->ell = 1.0;
+    o->windows = nullptr;
+    o->P = 0;
+    o->N = 32;
+    o->m = 4;
+    o->N_precise = 64;
+    o->m_precise = 6;
+    o->scale_features = 0;
+    o->cuda_stream = nullptr;
+}
+
+anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, double C, double tol,
+                           const svm_opts *opts_in, double *alpha_out, double *b_out, svm_stats *stats) {
+    try {
+        const auto t_start = std::chrono::steady_clock::now();
+        svm_opts o;
+        svm_opts_default(&o);
+        if (opts_in) o = *opts_in;
+        if (!X || !yh || !alpha_out || !b_out) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+        if (n < 2 || d < 1) return fail(ANOVA_ERR_INVALID_ARG, "need n >= 2 and d >= 1");
+        if (!(C > 0.0) || !std::isfinite(C)) return fail(ANOVA_ERR_INVALID_ARG, "C must be positive");
+        if (!(tol > 0.0)) return fail(ANOVA_ERR_INVALID_ARG, "tol must be positive");
+        if (o.max_iter < 1 || o.krylov_max < 1 || o.refine_max < 1 || !(o.sigma_barrier > 0 && o.sigma_barrier < 1) ||
+            !(o.gamma > 0 && o.gamma < 1) || !(o.krylov_tol > 0) || !(o.ell > 0))
+            return fail(ANOVA_ERR_INVALID_ARG, "invalid svm_opts");
+        bool has_pos = false, has_neg = false;
+        for (int64_t i = 0; i < n; ++i) {
+            if (yh[i] == 1.0) has_pos = true;
+            else if (yh[i] == -1.0) has_neg = true;
+            else return fail(ANOVA_ERR_INVALID_ARG, "labels must be -1 or +1");
+        }
+        if (!has_pos || !has_neg) return fail(ANOVA_ERR_INVALID_ARG, "both classes must occur");
+        // points (optionally min-max scaled) and windows
+        std::vector<double> Xs;
+        const double *Xp = X;
+        if (o.scale_features) {
+            Xs.assign(X, X + n * d);
+            for (int k = 0; k < d; ++k) {
+                double mn = INFINITY, mx = -INFINITY;
+                for (int64_t i = 0; i < n; ++i) {
+                    const double v = X[i * d + k];
+                    if (!std::isfinite(v)) return fail(ANOVA_ERR_NONFINITE, "points hold NaN or Inf");
+                    mn = std::min(mn, v);
+                    mx = std::max(mx, v);
+                }
+                for (int64_t i = 0; i < n; ++i)
+                    Xs[i * d + k] = mx > mn ? -kBoxHalf + 2 * kBoxHalf * (X[i * d + k] - mn) / (mx - mn) : 0.0;
+            }
+            Xp = Xs.data();
+        }
+        std::vector<int32_t> W;
+        int P = o.P;
+        if (o.windows) {
+            W.assign(o.windows, o.windows + 3 * P);
+        } else {
+            P = (d + 2) / 3;
+            W.assign(3 * P, -1);
+            for (int l = 0; l < P; ++l)
+                for (int k = 0; k < 3 && 3 * l + k < d; ++k) W[3 * l + k] = 3 * l + k;
+        }
+        std::vector<double> ell(std::max(P, 1), o.ell);
+        anova_plan *p32 = nullptr, *p64 = nullptr;
+        anova_status s;
+        if ((s = create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32, o.cuda_stream, &p32)) != ANOVA_OK)
+            return s;
+        std::unique_ptr<anova_plan, void (*)(anova_plan *)> g32(p32, destroy_plan);
+        if ((s = create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise, ANOVA_FP64,
+                             o.cuda_stream, &p64)) != ANOVA_OK)
+            return s;
+        std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64(p64, destroy_plan);
+        lowrank *lr = nullptr;
+        if ((s = lowrank_build_impl(p64, o.precond, (int)std::min<int64_t>(o.rank, n), o.err_tol, o.seed, &lr)) != ANOVA_OK)
+            return s;
+        std::unique_ptr<lowrank, void (*)(lowrank *)> glr(lr, lowrank_release);
+
+        Solver S;
+        S.p32 = p32;
+        S.p64 = p64;
+        S.lr = lr;
+        S.st = p64->stream;
+        S.n = n;
+        cudaStream_t st = S.st;
+        const long long N1 = n + 1;
+        // device vectors
+        std::vector<void *> bufs;
+        auto dalloc = [&](size_t bytes, void **ptr) -> bool {
+            if (cudaMalloc(ptr, bytes) != cudaSuccess) return false;
+            bufs.push_back(*ptr);
+            return true;
+        };
+        struct Freer {
+            std::vector<void *> &b;
+            ~Freer() {
+                for (void *x : b) cudaFree(x);
+            }
+        } freer{bufs};
+        double *dy, *dal, *dth, *df, *drhs, *ddelta, *dr, *dtmp, *dcorr, *dpart2;
+        double *work[10];
+        bool ok = dalloc(sizeof(double) * n, (void **)&dy) && dalloc(sizeof(double) * n, (void **)&dal) &&
+                  dalloc(sizeof(double) * n, (void **)&dth) && dalloc(sizeof(double) * n, (void **)&df) &&
+                  dalloc(sizeof(double) * N1, (void **)&drhs) && dalloc(sizeof(double) * N1, (void **)&ddelta) &&
+                  dalloc(sizeof(double) * N1, (void **)&dr) && dalloc(sizeof(double) * N1, (void **)&dtmp) &&
+                  dalloc(sizeof(double) * N1, (void **)&dcorr) && dalloc(sizeof(double) * kRedBlocks * 5, (void **)&S.part) &&
+                  dalloc(sizeof(double) * kRedBlocks * 5, (void **)&dpart2) &&
+                  dalloc(sizeof(float) * n, (void **)&S.t32) && dalloc(sizeof(float) * n, (void **)&S.k32) &&
+                  dalloc(sizeof(double) * n, (void **)&S.t64) && dalloc(sizeof(double) * n, (void **)&S.k64);
+        for (int k = 0; k < 10 && ok; ++k) ok = dalloc(sizeof(double) * N1, (void **)&work[k]);
+        if (!ok) return fail(ANOVA_ERR_OOM, "solver allocation failed");
+        S.y = dy;
+        S.theta = dth;
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(dy, yh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        const int nb = blocks_for(n);
+        // Algorithm 1: alpha^0 = C/2, lambda^0 = 0, mu_0 = 1
+        k_fill_d<<<nb, 256, 0, st>>>(dal, n, C / 2.0);
+        double lam = 0.0, mu = 1.0;
+        if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
+        std::vector<double> hp(kRedBlocks * 5);
+        auto objectives = [&](double *sums) -> anova_status {
+            k_objective_partial<<<nb, 256, 0, st>>>(dal, dy, df, -lam, lam, mu, C, n, dpart2);
+            ANOVA_CUDA_TRY(cudaGetLastError());
+            ANOVA_CUDA_TRY(cudaMemcpyAsync(hp.data(), dpart2, sizeof(double) * 5 * nb, cudaMemcpyDeviceToHost, st));
+            ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int k = 0; k < 5; ++k) {
+                double acc = 0.0;
+                for (int i = 0; i < nb; ++i) acc += hp[k * nb + i];
+                sums[k] = acc;
+            }
+            return ANOVA_OK;
+        };
+        double sums[5];
+        if ((s = objectives(sums)) != ANOVA_OK) return s;
+        const double nxa0 = std::max(1.0, std::fabs(sums[3]));
+        const double nxl0 = std::max(1.0, std::sqrt(sums[4]));
+        double dual = sums[0] - 0.5 * sums[1], primal = 0.5 * sums[1] + C * sums[2];
+        double xa = std::fabs(sums[3]) / nxa0, xl = std::sqrt(sums[4]) / nxl0;
+        int it = 0;
+        bool converged = false;
+        auto done = [&]() {
+            if (o.stop == SVM_STOP_ALG1) return !(mu > tol || xa > tol || xl > tol);
+            if (it == 0) return false;
+            return (primal - dual) / std::max(1.0, std::fabs(primal)) <= tol && xa <= tol;
+        };
+        std::vector<double> hstep(kRedBlocks);
+        while (it < o.max_iter) {
+            if (done()) {
+                converged = true;
+                break;
+            }
+            mu *= o.sigma_barrier;
+            k_theta<<<nb, 256, 0, st>>>(dal, mu, C, n, dth);
+            k_newton_rhs<<<nb, 256, 0, st>>>(dal, dy, df, lam, mu, C, n, drhs);
+            k_dot<<<nb, 256, 0, st>>>(dy, dal, n, S.part);
+            k_sum_to<<<1, 32, 0, st>>>(S.part, nb, 1.0, drhs + n);  // y^T alpha
+            ANOVA_CUDA_TRY(cudaGetLastError());
+            if ((s = lowrank_set_theta_impl(lr, dth, dy)) != ANOVA_OK) return s;
+            // Newton direction: MINRES on the FP32 operator, refined with FP64 residuals
+            double gnorm2;
+            if ((s = S.dot(drhs, drhs, N1, &gnorm2)) != ANOVA_OK) return s;
+            const double gnorm = std::sqrt(gnorm2);
+            ANOVA_CUDA_TRY(cudaMemsetAsync(ddelta, 0, sizeof(double) * N1, st));
+            ANOVA_CUDA_TRY(cudaMemcpyAsync(dr, drhs, sizeof(double) * N1, cudaMemcpyDeviceToDevice, st));
+            const double inner_tol = std::max(o.krylov_tol, 1e-6);
+            for (int k = 0; k < o.refine_max; ++k) {
+                int iters = 0;
+                if ((s = minres(S, dr, dcorr, inner_tol, o.krylov_max, work, &iters)) != ANOVA_OK) return s;
+                k_axpy<<<blocks_for(N1), 256, 0, st>>>(1.0, dcorr, N1, ddelta);
+                if ((s = S.apply(ddelta, dtmp, true)) != ANOVA_OK) return s;
+                k_sub<<<blocks_for(N1), 256, 0, st>>>(drhs, dtmp, N1, dr);
+                S.refine_total += 1;
+                double rn2;
+                if ((s = S.dot(dr, dr, N1, &rn2)) != ANOVA_OK) return s;
+                if (std::sqrt(rn2) <= o.krylov_tol * gnorm) break;
+            }
+            // step to the boundary (Algorithm 1: s_alpha = s_lambda, times gamma_0)
+            k_step_partial<<<nb, 256, 0, st>>>(dal, ddelta, C, n, S.part);
+            ANOVA_CUDA_TRY(cudaGetLastError());
+            ANOVA_CUDA_TRY(cudaMemcpyAsync(hstep.data(), S.part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+            double dlam = 0.0;
+            ANOVA_CUDA_TRY(cudaMemcpyAsync(&dlam, ddelta + n, sizeof(double), cudaMemcpyDeviceToHost, st));
+            ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+            double smax = 1.0;
+            for (int i = 0; i < nb; ++i) smax = std::min(smax, hstep[i]);
+            const double step = o.gamma * smax;
+            k_axpy<<<nb, 256, 0, st>>>(step, ddelta, n, dal);
+            lam += step * dlam;
+            if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
+            ++it;
+            if ((s = objectives(sums)) != ANOVA_OK) return s;
+            dual = sums[0] - 0.5 * sums[1];
+            primal = 0.5 * sums[1] + C * sums[2];
+            xa = std::fabs(sums[3]) / nxa0;
+            xl = std::sqrt(sums[4]) / nxl0;
+            if (!std::isfinite(dual) || !std::isfinite(primal))
+                return fail(ANOVA_ERR_NONFINITE, "interior point iterate is not finite");
+        }
+        if (!converged && done()) converged = true;
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(alpha_out, dal, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        *b_out = -lam;
+        if (stats) {
+            stats->iterations = it;
+            stats->krylov_iterations = S.krylov_total;
+            stats->refinements = S.refine_total;
+            stats->rank = lr->rank;
+            stats->converged = converged ? 1 : 0;
+            stats->mu = mu;
+            stats->dual = dual;
+            stats->primal = primal;
+            stats->rel_gap = (primal - dual) / std::max(1.0, std::fabs(primal));
+            stats->xi_alpha = xa;
+            stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        }
+        if (!converged) return fail(ANOVA_ERR_NOT_CONVERGED, "interior point method reached max_iter");
+        return ANOVA_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ANOVA_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(ANOVA_ERR_INVALID_ARG, "unexpected exception");
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+"""Parity of the device low-rank preconditioners (Secs. 4-5) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import kernel as ok
+from oracle import precond as op
+from synth import minmax_scale, consecutive_windows
+
+from ._gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return require_gpu()
+
+
+def _setup(ab, n=300, d=6, ell=0.5, seed=1, binary=False):
+    rng = np.random.default_rng(seed)
+    if binary:
+        X = minmax_scale(rng.integers(0, 2, size=(n, d)).astype(float))
+    else:
+        X = minmax_scale(rng.standard_normal((n, d)))
+    W = consecutive_windows(d)
+    plan = ab.anova_nfft_plan(X, W, ell, N=64, m=6, flags=ab.ANOVA_FP64)
+    K = ok.anova_kernel_matrix(X, W, ell)
+    return X, W, plan, K, rng
+
+
+def _factor(torch, ab, lr, n):
+    rank, piv = ab.lowrank_info(lr)
+    L = torch.empty((rank, n), dtype=torch.float64, device="cuda")
+    ab.lowrank_factor(lr, L)
+    return L.cpu().numpy().T, piv
+
+
+def test_pivoted_cholesky_matches_algorithm2(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, 25, 0.0)
+    L, piv = _factor(torch, ab, lr, 300)
+    Lo, pivo = op.pivoted_cholesky(K, 25)
+    assert L.shape == (300, 25)
+    assert np.array_equal(piv, pivo)
+    assert np.allclose(L, Lo, rtol=0, atol=1e-10)
+
+
+def test_pivoted_cholesky_full_rank_and_err_tol(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=80, ell=0.05)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, 80, 0.0)
+    L, _ = _factor(torch, ab, lr, 80)
+    assert np.allclose(L @ L.T, K, rtol=0, atol=1e-10 * np.max(K))
+    X2, W2, plan2, K2, _ = _setup(ab, n=200, d=3, ell=2.0)
+    lr2 = ab.lowrank_precond_build(plan2, ab.PCHOL_GREEDY, 200, 1e-5)
+    L2, _ = _factor(torch, ab, lr2, 200)
+    assert L2.shape[1] < 40
+    assert np.max(np.diag(K2 - L2 @ L2.T)) <= 1e-5 * np.max(np.diag(K2)) + 1e-13
+
+
+def test_rank_of_duplicate_heavy_window(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=400, d=3, ell=0.3, binary=True)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, 50, 1e-10)
+    L, _ = _factor(torch, ab, lr, 400)
+    assert L.shape[1] == 8
+    assert np.allclose(L @ L.T, K, atol=1e-9)
+
+
+def test_nystrom_on_pivot_set(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=250, seed=3)
+    lr = ab.lowrank_precond_build(plan, ab.NYSTROM, 20, 0.0)
+    Z, piv = _factor(torch, ab, lr, 250)
+    Zo = op.nystrom_columns(K, piv)
+    assert np.allclose(Z @ Z.T, Zo @ Zo.T, rtol=0, atol=1e-8 * np.max(K))
+    assert np.allclose((Z @ Z.T)[:, piv], K[:, piv], atol=1e-8)
+
+
+def test_woodbury_block_preconditioner(env):
+    torch, ab = env
+    X, W, plan, K, rng = _setup(ab, n=500, seed=4)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, 30, 0.0)
+    L, _ = _factor(torch, ab, lr, 500)
+    L32 = L.astype(np.float32).astype(np.float64)   # the apply uses the FP32 panel
+    y = np.where(rng.standard_normal(500) >= 0, 1.0, -1.0)
+    theta = np.exp(rng.uniform(-4, 4, 500))
+    g = rng.standard_normal(501)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    th, yy, gg = dev(theta), dev(y), dev(g)
+    x = torch.empty(501, dtype=torch.float64, device="cuda")
+    ab.lowrank_precond_set_theta(lr, th, yy)
+    ab.lowrank_precond_apply(lr, th, yy, gg, x)
+    torch.cuda.synchronize()
+    s = y @ op.woodbury_apply(L32, theta, y, y)
+    ref = op.blockdiag_apply(L32, theta, y, g, s)
+    got = x.cpu().numpy()
+    assert np.allclose(got, ref, rtol=1e-8, atol=1e-10 * np.max(np.abs(ref)))
+    # and against the dense inverse of A^ with the same factor
+    dense = np.linalg.solve(op.dense_Ahat(L32, theta, y), g[:500])
+    assert np.allclose(got[:500], dense, rtol=1e-7, atol=1e-9 * np.max(np.abs(dense)))
