@@ -10,10 +10,16 @@ Barrier Lagrangian and optimality conditions: Sec. 2. Newton system: Sec. 2, eq.
     Theta = diag(mu (1/a^2 + 1/(C - a)^2)).
 
 Readings of points the paper leaves open:
-* initial point (C-7): alpha^0 = (C/2) e, lambda^0 = 0; relative infeasibilities are divided by
-  max(1, ||xi^0||) so that a zero xi^0 (balanced labels) does not divide by zero.
-* barrier schedule (C-8): constant sigma = 0.6 (Table 1), applied before the Newton solve, so
-  Theta and the right-hand side use mu_{it+1}.
+* initial point: alpha^0 = min(C/2, 1/2) e, lambda^0 = 0 (the paper only asks for non-zero
+  initial infeasibilities); relative infeasibilities are divided by max(1, ||xi^0||) so that a
+  zero xi^0 (balanced labels) does not divide by zero.
+* barrier schedule: Sec. 2 reduces mu either by a constant sigma or by a sigma_it that changes
+  every iteration. sigma_rule="constant" is mu <- 0.6 mu (Table 1); sigma_rule="adaptive" (the
+  default) is sigma_it = 1 - (1 - 0.6) s_{it-1} with s_{it-1} the previous step length (s_{-1} =
+  1), which equals the constant rule while full steps are taken and keeps mu while the step is
+  short. With the constant rule and alpha^0 = C/2 the method stalls at the boundary for C = 10 or
+  100 even with exact solves. Either way mu is reduced before the Newton solve, so Theta and the
+  right-hand side use mu_{it+1}.
 * step lengths (C-9): s = gamma_0 * max{s <= 1 : 0 <= alpha + s d_alpha <= C}; s_lambda = s_alpha.
 * stopping: stop="alg1" is Algorithm 1's loop test (continue while mu > tol or either relative
   infeasibility is above tol); stop="gap" is reading C-10 (stop once the relative duality gap
@@ -65,7 +71,7 @@ def step_to_boundary(alpha, dalpha, C):
 
 
 def ipm_dense(K, y, C, tol=1e-6, sigma=0.6, gamma0=0.99995, mu0=1.0, max_iter=100,
-              record=None, stop="gap"):
+              record=None, stop="gap", sigma_rule="adaptive", alpha0=None):
     """Algorithm 1 with the Newton system solved by a dense LU (numpy.linalg.solve).
 
     Returns dict(alpha, lam, b, iterations, mu, history, reason)."""
@@ -73,9 +79,10 @@ def ipm_dense(K, y, C, tol=1e-6, sigma=0.6, gamma0=0.99995, mu0=1.0, max_iter=10
     y = np.asarray(y, dtype=np.float64)
     n = y.size
     Q = (y[:, None] * K) * y[None, :]
-    alpha = np.full(n, C / 2.0)
+    alpha = np.full(n, min(C / 2.0, 0.5) if alpha0 is None else alpha0)
     lam = 0.0
     mu = mu0
+    s_prev = 1.0
     xl0, xa0 = newton_rhs(Q, y, alpha, lam, mu, C)
     nxl0 = max(1.0, float(np.linalg.norm(xl0)))
     nxa0 = max(1.0, abs(xa0))
@@ -99,7 +106,7 @@ def ipm_dense(K, y, C, tol=1e-6, sigma=0.6, gamma0=0.99995, mu0=1.0, max_iter=10
         if np.any(alpha <= 0.0) or np.any(alpha >= C):
             reason = "bound"
             break
-        mu = sigma * mu
+        mu = (sigma if sigma_rule == "constant" else 1.0 - (1.0 - sigma) * s_prev) * mu
         theta = mu * (1.0 / alpha ** 2 + 1.0 / (C - alpha) ** 2)
         r1, r2 = newton_rhs(Q, y, alpha, lam, mu, C)
         A = np.zeros((n + 1, n + 1))
@@ -109,6 +116,7 @@ def ipm_dense(K, y, C, tol=1e-6, sigma=0.6, gamma0=0.99995, mu0=1.0, max_iter=10
         sol = np.linalg.solve(A, np.concatenate([r1, [r2]]))
         da, dl = sol[:n], sol[n]
         s = gamma0 * step_to_boundary(alpha, da, C)
+        s_prev = s
         alpha = alpha + s * da
         lam = lam + s * dl
         xl, xa = newton_rhs(Q, y, alpha, lam, mu, C)

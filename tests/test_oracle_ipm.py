@@ -63,7 +63,8 @@ def test_algorithm1_loop_test_stops_on_mu_and_infeasibilities():
     K = ok.anova_kernel_matrix(cfg["X"], cfg["windows"], cfg["sigma"])
     # Table 1: tol_ip = 1e-1. (The relative xi_lambda plateaus near 1e-2 with a constant sigma = 0.6,
     # so the loop test cannot reach much smaller tolerances; the gap test is used for those.)
-    res = oi.ipm_dense(K, cfg["y"], cfg["C"], tol=1e-1, stop="alg1", max_iter=50)
+    res = oi.ipm_dense(K, cfg["y"], cfg["C"], tol=1e-1, stop="alg1", max_iter=50,
+                       sigma_rule="constant")
     assert res["reason"] == "converged"
     assert res["mu"] <= 1e-1
     # mu is reduced by the constant factor 0.6 once per iteration from mu0 = 1
@@ -97,3 +98,30 @@ def test_step_to_boundary():
     assert oi.step_to_boundary(a, np.array([-1.0, 0.0, 0.0]), 1.0) == pytest.approx(0.5)
     assert oi.step_to_boundary(a, np.array([0.0, 2.0, 0.0]), 1.0) == pytest.approx(0.25)
     assert oi.step_to_boundary(a, np.array([0.1, -0.1, 0.0]), 1.0) == 1.0
+
+
+@pytest.mark.parametrize("C", [10.0, 100.0])
+def test_adaptive_barrier_converges_for_large_C(C):
+    """Sec. 2 allows a sigma_it that changes every iteration; with it the method reaches the
+    optimum for large C, where the constant rule stalls at the boundary."""
+    rng = np.random.default_rng(int(C))
+    n = 8
+    X = minmax_scale(rng.standard_normal((n, 3)))
+    y = np.array([1.0, -1.0, 1.0, 1.0, -1.0, -1.0, 1.0, -1.0])
+    K = ok.anova_kernel_matrix(X, consecutive_windows(3), 0.3)
+    best, _ = oi.brute_force_dual(K, y, C)
+    res = oi.ipm_dense(K, y, C, tol=1e-12, max_iter=300)
+    assert res["reason"] == "converged"
+    assert oi.dual_objective(K, y, res["alpha"]) == pytest.approx(best, rel=1e-8, abs=1e-9)
+
+
+def test_adaptive_rule_equals_constant_rule_with_full_steps():
+    # workload-1-like data at C = 1: every step is a full step after the first two, so both
+    # rules reduce mu by 0.6 there and reach the same optimum
+    cfg = config1(n=150)
+    K = ok.anova_kernel_matrix(cfg["X"], cfg["windows"], cfg["sigma"])
+    a = oi.ipm_dense(K, cfg["y"], 1.0, tol=1e-9, max_iter=200, sigma_rule="constant")
+    b = oi.ipm_dense(K, cfg["y"], 1.0, tol=1e-9, max_iter=200)
+    da = oi.dual_objective(K, cfg["y"], a["alpha"])
+    db = oi.dual_objective(K, cfg["y"], b["alpha"])
+    assert da == pytest.approx(db, rel=1e-7)
