@@ -70,14 +70,24 @@ enum {
     SVM_STOP_ALG1 = 1  /* Algorithm 1's test: mu and both relative infeasibilities below tol */
 };
 
+/* Barrier schedules (Sec. 2: mu is reduced by a constant sigma or by a sigma_it per iteration). */
+enum {
+    SVM_SIGMA_CONSTANT = 0,  /* mu <- sigma mu */
+    SVM_SIGMA_ADAPTIVE = 1   /* mu <- (1 - (1 - sigma) s_prev) mu, s_prev = last step (default) */
+};
+
 typedef struct {
     int max_iter;            /* interior point iterations (Table 1: 50) */
     double sigma_barrier;    /* barrier reduction mu <- sigma mu (Table 1: 0.6) */
     double gamma;            /* step factor to the boundary (Table 1: 0.99995) */
+    int sigma_rule;          /* SVM_SIGMA_ADAPTIVE (default) or SVM_SIGMA_CONSTANT */
+    double alpha0;           /* initial alpha_i; <= 0 selects min(C/2, 1/2) */
     int stop;                /* SVM_STOP_GAP or SVM_STOP_ALG1 */
     int krylov_max;          /* MINRES iterations per solve (Table 1: 100) */
     double krylov_tol;       /* relative residual of each Newton solve (default 1e-8) */
-    int refine_max;          /* FP64 refinement passes per Newton solve (default 4) */
+    int refine_max;          /* FP64 refinement passes per Newton solve (default 4); when the
+                                FP32-operator passes stop reducing the FP64 residual, the solve
+                                finishes with MINRES on the FP64 operator */
     int precond;             /* PCHOL_GREEDY or NYSTROM */
     int rank;                /* preconditioner rank (default 200, at most n) */
     double err_tol;          /* pivoted-Cholesky tolerance (Table 1: 1e-5) */
@@ -95,6 +105,7 @@ typedef struct {
     int iterations;          /* interior point iterations done */
     int krylov_iterations;   /* MINRES iterations over all Newton solves */
     int refinements;         /* refinement passes over all Newton solves */
+    int fp64_krylov_iterations; /* MINRES iterations run on the FP64 operator (fallback) */
     int rank;                /* preconditioner rank */
     int converged;           /* 1 if the stopping rule was met */
     double mu;               /* final barrier parameter */

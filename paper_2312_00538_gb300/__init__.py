@@ -287,11 +287,14 @@ def anova_version():
 # --------------------------------------------------------------------------- solver (anova_svm.h)
 SVM_STOP_GAP = 0
 SVM_STOP_ALG1 = 1
+SVM_SIGMA_CONSTANT = 0
+SVM_SIGMA_ADAPTIVE = 1
 
 
 class svm_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("sigma_barrier", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("stop", ctypes.c_int), ("krylov_max", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("sigma_rule", ctypes.c_int), ("alpha0", ctypes.c_double),
+                ("stop", ctypes.c_int), ("krylov_max", ctypes.c_int),
                 ("krylov_tol", ctypes.c_double), ("refine_max", ctypes.c_int),
                 ("precond", ctypes.c_int), ("rank", ctypes.c_int), ("err_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("ell", ctypes.c_double),
@@ -303,7 +306,8 @@ class svm_opts(ctypes.Structure):
 
 class svm_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
-                ("refinements", ctypes.c_int), ("rank", ctypes.c_int), ("converged", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("fp64_krylov_iterations", ctypes.c_int),
+                ("rank", ctypes.c_int), ("converged", ctypes.c_int),
                 ("mu", ctypes.c_double), ("dual", ctypes.c_double), ("primal", ctypes.c_double),
                 ("rel_gap", ctypes.c_double), ("xi_alpha", ctypes.c_double),
                 ("time_ms", ctypes.c_double)]

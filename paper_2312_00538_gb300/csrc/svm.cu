@@ -188,7 +188,7 @@ struct Solver {
     std::vector<double> hpart;
     float *t32 = nullptr, *k32 = nullptr;
     double *t64 = nullptr, *k64 = nullptr;
-    int krylov_total = 0, refine_total = 0;
+    int krylov_total = 0, refine_total = 0, fp64_krylov_total = 0;
 
     anova_status dot(const double *a, const double *b, long long len, double *out) {
         const int nb = blocks_for(len);
@@ -233,7 +233,8 @@ struct Solver {
 };
 
 // Preconditioned MINRES (Paige-Saunders) for A x = b, x0 = 0, vectors of length n + 1.
-anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxit, double *work[10], int *iters) {
+anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxit, double *work[10], int *iters,
+                    bool precise = false) {
     const long long N1 = S.n + 1;
     const int nb = blocks_for(N1);
     double *r_prev = work[0], *r_cur = work[1], *r_next = work[2], *y_cur = work[3], *y_next = work[4];
@@ -256,7 +257,7 @@ anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxi
     double c_prev2 = 1.0, s_prev2 = 0.0, c_prev = 1.0, s_prev = 0.0;
     for (int it = 1; it <= maxit; ++it) {
         k_scale<<<nb, 256, 0, st>>>(y_cur, 1.0 / beta, N1, v);
-        if ((s = S.apply(v, Av, false)) != ANOVA_OK) return s;
+        if ((s = S.apply(v, Av, precise)) != ANOVA_OK) return s;
         double alpha;
         if ((s = S.dot(v, Av, N1, &alpha)) != ANOVA_OK) return s;
         k_lin3<<<nb, 256, 0, st>>>(Av, r_cur, r_prev, -alpha / beta, beta_prev > 0 ? -beta / beta_prev : 0.0, N1, r_next);
@@ -289,7 +290,8 @@ anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxi
         *iters = it;
         if (std::fabs(phibar) <= rtol * beta1 || beta == 0.0) break;
     }
-    S.krylov_total += *iters;
+    if (precise) S.fp64_krylov_total += *iters;
+    else S.krylov_total += *iters;
     return ANOVA_OK;
 }
 
@@ -348,6 +350,8 @@ void svm_opts_default(svm_opts *o) {
     o->max_iter = 50;
     o->sigma_barrier = 0.6;
     o->gamma = 0.99995;
+    o->sigma_rule = SVM_SIGMA_ADAPTIVE;
+    o->alpha0 = 0.0;
     o->stop = SVM_STOP_GAP;
     o->krylov_max = 100;
     o->krylov_tol = 1e-8;
@@ -468,9 +472,11 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         S.theta = dth;
         ANOVA_CUDA_TRY(cudaMemcpyAsync(dy, yh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
         const int nb = blocks_for(n);
-        // Algorithm 1: alpha^0 = C/2, lambda^0 = 0, mu_0 = 1
-        k_fill_d<<<nb, 256, 0, st>>>(dal, n, C / 2.0);
-        double lam = 0.0, mu = 1.0;
+        // Algorithm 1: alpha^0 (default min(C/2, 1/2)), lambda^0 = 0, mu_0 = 1
+        const double a0 = o.alpha0 > 0.0 ? o.alpha0 : std::min(C / 2.0, 0.5);
+        if (!(a0 < C)) return fail(ANOVA_ERR_INVALID_ARG, "alpha0 must lie in (0, C)");
+        k_fill_d<<<nb, 256, 0, st>>>(dal, n, a0);
+        double lam = 0.0, mu = 1.0, s_prev = 1.0;
         if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
         std::vector<double> hp(kRedBlocks * 5);
         auto objectives = [&](double *sums) -> anova_status {
@@ -504,7 +510,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                 converged = true;
                 break;
             }
-            mu *= o.sigma_barrier;
+            mu *= o.sigma_rule == SVM_SIGMA_CONSTANT ? o.sigma_barrier : 1.0 - (1.0 - o.sigma_barrier) * s_prev;
             k_theta<<<nb, 256, 0, st>>>(dal, mu, C, n, dth);
             k_newton_rhs<<<nb, 256, 0, st>>>(dal, dy, df, lam, mu, C, n, drhs);
             k_dot<<<nb, 256, 0, st>>>(dy, dal, n, S.part);
@@ -518,6 +524,8 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             ANOVA_CUDA_TRY(cudaMemsetAsync(ddelta, 0, sizeof(double) * N1, st));
             ANOVA_CUDA_TRY(cudaMemcpyAsync(dr, drhs, sizeof(double) * N1, cudaMemcpyDeviceToDevice, st));
             const double inner_tol = std::max(o.krylov_tol, 1e-6);
+            double rel_prev = 1.0;
+            bool solved = false;
             for (int k = 0; k < o.refine_max; ++k) {
                 int iters = 0;
                 if ((s = minres(S, dr, dcorr, inner_tol, o.krylov_max, work, &iters)) != ANOVA_OK) return s;
@@ -527,7 +535,25 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                 S.refine_total += 1;
                 double rn2;
                 if ((s = S.dot(dr, dr, N1, &rn2)) != ANOVA_OK) return s;
-                if (std::sqrt(rn2) <= o.krylov_tol * gnorm) break;
+                const double rel = std::sqrt(rn2) / gnorm;
+                if (rel <= o.krylov_tol) {
+                    solved = true;
+                    break;
+                }
+                if (rel > 0.5 * rel_prev) break;  // the FP32 operator no longer reduces the residual
+                rel_prev = rel;
+            }
+            if (!solved) {
+                // finish on the FP64 operator (same preconditioner) from the current direction
+                double rn2;
+                if ((s = S.dot(dr, dr, N1, &rn2)) != ANOVA_OK) return s;
+                const double rel = std::sqrt(rn2) / gnorm;
+                if (rel > o.krylov_tol) {
+                    int iters = 0;
+                    if ((s = minres(S, dr, dcorr, o.krylov_tol / rel, o.krylov_max, work, &iters, true)) != ANOVA_OK)
+                        return s;
+                    k_axpy<<<blocks_for(N1), 256, 0, st>>>(1.0, dcorr, N1, ddelta);
+                }
             }
             // step to the boundary (Algorithm 1: s_alpha = s_lambda, times gamma_0)
             k_step_partial<<<nb, 256, 0, st>>>(dal, ddelta, C, n, S.part);
@@ -539,6 +565,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             double smax = 1.0;
             for (int i = 0; i < nb; ++i) smax = std::min(smax, hstep[i]);
             const double step = o.gamma * smax;
+            s_prev = step;
             k_axpy<<<nb, 256, 0, st>>>(step, ddelta, n, dal);
             lam += step * dlam;
             if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
@@ -559,6 +586,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             stats->iterations = it;
             stats->krylov_iterations = S.krylov_total;
             stats->refinements = S.refine_total;
+            stats->fp64_krylov_iterations = S.fp64_krylov_total;
             stats->rank = lr->rank;
             stats->converged = converged ? 1 : 0;
             stats->mu = mu;

@@ -61,3 +61,20 @@ def test_config1_dual_objective(env):
     # the solver's own FP64-plan objective agrees with the exact one
     assert abs(st["dual"] - d_gpu) <= 1e-8 * abs(d_gpu)
     assert oi.kkt_violation(K, y, alpha, b, C, eps_bound=1e-4) <= 5e-2
+
+
+@pytest.mark.parametrize("C", [10.0, 100.0])
+def test_large_C_workload3_like(env, C):
+    """Workload-3-like data (Gaussian + binary features, tanh teacher, 5 % flips) at large C,
+    where the barrier factor has to adapt to short steps (Sec. 2, sigma_it)."""
+    torch, ab = env
+    from synth import config3
+    cfg = config3(n=1500)
+    X, y, W = cfg["X"], cfg["y"], cfg["windows"]
+    alpha, b, st, status = _solve(ab, X, y, W, C, 1e-6, rank=100, krylov_tol=1e-8)
+    assert status == ab.ANOVA_OK, st
+    K = ok.anova_kernel_matrix(X, W, 1.0)
+    ref = oi.ipm_dense(K, y, C, tol=1e-9, max_iter=300)
+    d_gpu = oi.dual_objective(K, y, alpha)
+    d_ref = oi.dual_objective(K, y, ref["alpha"])
+    assert abs(d_gpu - d_ref) <= 1e-6 * abs(d_ref)
