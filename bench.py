@@ -183,7 +183,7 @@ def profile_traffic(kernel_key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None when
     the summary is missing or was taken on a different kernel source."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "matvec_n1e6_fp32_traffic.txt")
     try:
         with open(path) as f:
             rec = json.load(f)

@@ -183,12 +183,12 @@ struct SpreadX2Cfg {
     static constexpr int TW = B + W2 - 1;
     static constexpr int TV = TW * TW * TW;
     static constexpr int TVP = (TV + 3) / 4 * 4;
-    static constexpr int XO = 0, YO = 2 * W2, ZO = 4 * W2, PS = 5 * W2;  // staged floats per point
+    static constexpr int XO = 0, YO = W2, ZO = 2 * W2, PS = 3 * W2;      // staged floats per point
     static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS);
 };
 
 template <int M, int B, int NWARP>
-__global__ void __launch_bounds__(NWARP * 32) k_spread3_x2(SpreadArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
     using C = SpreadX2Cfg<M, B, NWARP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
     static_assert(16 % W2 == 0 && RPL * 16 == W2 * W2, "2M must divide 16");
@@ -208,24 +208,14 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread3_x2(SpreadArgs a) {
     for (int i = threadIdx.x; i < NWARP * C::TVP; i += NWARP * 32) tiles_s[i] = 0.0f;
     __syncthreads();
 
-    // each warp takes whole cells: the segments starting in its share of the item's points
-    // (split at segment boundaries, so no cell is divided between warps)
+    // each warp takes an equal share of the item's points (a cell may be split between two
+    // warps; each adds its part into its own tile)
     const int4 s_first = a.segs[wi.y];
     const int4 s_last = a.segs[wi.z - 1];
     const int p0 = s_first.y, p1 = s_last.y + s_last.z;
     const int len = p1 - p0;
-    auto first_seg_from = [&](int target) {
-        int lo = wi.y, hi = wi.z;  // first segment with start >= target (wi.z if none)
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (a.segs[mid].y >= target) hi = mid; else lo = mid + 1;
-        }
-        return lo;
-    };
-    const int sw0 = warp == 0 ? wi.y : first_seg_from(p0 + (int)(((long long)len * warp) / NWARP));
-    const int sw1 = warp == NWARP - 1 ? wi.z : first_seg_from(p0 + (int)(((long long)len * (warp + 1)) / NWARP));
-    const int pw0 = sw0 < wi.z ? a.segs[sw0].y : p1;
-    const int pw1 = sw1 < wi.z ? a.segs[sw1].y : p1;
+    const int pw0 = p0 + (int)(((long long)len * warp) / NWARP);
+    const int pw1 = p0 + (int)(((long long)len * (warp + 1)) / NWARP);
 
     const float *fr0 = reinterpret_cast<const float *>(a.frac);
     const float *fr1 = fr0 + a.total, *fr2 = fr0 + 2 * a.total;
@@ -236,7 +226,15 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread3_x2(SpreadArgs a) {
     const int rb = lh % W2;
 
     if (pw0 < pw1) {
-        int s = sw0;
+        int s;
+        {
+            int lo = wi.y, hi = wi.z - 1;  // last segment starting at or before pw0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.segs[mid].y <= pw0) lo = mid; else hi = mid - 1;
+            }
+            s = lo;
+        }
         int4 sg = a.segs[s];
         int4 sg_next = (s + 1 < wi.z) ? a.segs[s + 1] : sg;
         int q = pw0;
@@ -291,33 +289,46 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread3_x2(SpreadArgs a) {
 #pragma unroll
                 for (int j = 0; j < W2; ++j) wz[j] *= vl;
                 float4 *dst = reinterpret_cast<float4 *>(wts + lane * PS);
+                // X at permuted positions a -> (a % S) * RPL + a / S, so a lane's rows are adjacent
 #pragma unroll
-                for (int pos = 0; pos < W2; pos += 2) {
-                    const int a0 = (pos % RPL) * S + pos / RPL, a1 = ((pos + 1) % RPL) * S + (pos + 1) / RPL;
-                    dst[(C::XO / 4) + pos / 2] = make_float4(wx[a0], wx[a0], wx[a1], wx[a1]);
+                for (int pos = 0; pos < W2; pos += 4) {
+                    float xv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) xv[t] = wx[((pos + t) % RPL) * S + (pos + t) / RPL];
+                    dst[(C::XO + pos) / 4] = make_float4(xv[0], xv[1], xv[2], xv[3]);
                 }
 #pragma unroll
-                for (int b = 0; b < W2; b += 2) dst[(C::YO / 4) + b / 2] = make_float4(wy[b], wy[b], wy[b + 1], wy[b + 1]);
+                for (int b = 0; b < W2; b += 4) dst[(C::YO + b) / 4] = make_float4(wy[b], wy[b + 1], wy[b + 2], wy[b + 3]);
 #pragma unroll
-                for (int c = 0; c < W2; c += 4) dst[(C::ZO / 4) + c / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
+                for (int c = 0; c < W2; c += 4) dst[(C::ZO + c) / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
             }
             __syncwarp();
             const int npair = (cnt + 1) >> 1;
 #pragma unroll 2
             for (int jj = 0; jj < npair; ++jj) {
                 const float *pw = wts + (2 * jj + half) * PS;
-                f32x2 xr[RPL], z2[W2 / 2];
-                const f32x2 y2 = *reinterpret_cast<const f32x2 *>(pw + C::YO + 2 * rb);
+                float xr[RPL];
+                f32x2 z2[W2 / 2];
+                const float yb = pw[C::YO + rb];
+                if constexpr (RPL % 4 == 0) {
 #pragma unroll
-                for (int k = 0; k < RPL; k += 2) {
-                    if (k + 1 < RPL) lds_pairs(pw + C::XO + 2 * (g * RPL + k), xr[k], xr[k + 1]);
-                    else xr[k] = *reinterpret_cast<const f32x2 *>(pw + C::XO + 2 * (g * RPL + k));
+                    for (int k = 0; k < RPL; k += 4) {
+                        const float4 t = *reinterpret_cast<const float4 *>(pw + C::XO + g * RPL + k);
+                        xr[k] = t.x;
+                        xr[k + 1] = t.y;
+                        xr[k + 2] = t.z;
+                        xr[k + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) xr[k] = pw[C::XO + g * RPL + k];
                 }
 #pragma unroll
                 for (int c = 0; c < W2 / 2; c += 2) lds_pairs(pw + C::ZO + 2 * c, z2[c], z2[c + 1]);
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) {
-                    const f32x2 rw = mul2(xr[k], y2);
+                    const float rs = xr[k] * yb;
+                    const f32x2 rw = make_float2(rs, rs);
 #pragma unroll
                     for (int c = 0; c < W2 / 2; ++c) acc[k][c] = fma2(rw, z2[c], acc[k][c]);
                 }
