@@ -18,6 +18,7 @@ constexpr double kBoxHalf = 0.2;       // points in [-0.2, 0.2]
 constexpr int kSegMax = 256;           // points per segment (one cell, split at this size)
 constexpr int kWiMax = 2048;           // points per spread work item (one bin)
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
+constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
 
 // ----------------------------------------------------------------------------- host maths
@@ -92,6 +93,7 @@ struct anova_plan {
     int nseg = 0, nwi = 0, ntiles = 0;
     int64_t grid_total = 0;               // elements of all windows' grids (one RHS)
     std::vector<double> poly;             // window polynomial coefficients (FP32 kernels)
+    std::vector<double> poly64;           // window polynomial coefficients (FP64 kernels)
 
     // device memory
     void *frac = nullptr;         // T[3][P*n]: fractional cell offsets, sorted per window

@@ -11,9 +11,10 @@ namespace anova {
 // Window polynomial coefficients (FP32 kernels) and Kaiser-Bessel constants (FP64 kernels),
 // passed by value so that they live in the kernel-parameter constant bank.
 struct WinParams {
-    float c[16][kPolyDeg + 1];  // c[j][p]: psi(f + m - 1 - j) ~ sum_p c z^p, z = 2f - 1
-    double beta;                // Kaiser-Bessel shape pi (2 - 1/oversampling)
-    double scale;               // m / sinh(beta m): normalises psi(0) to 1
+    float c[16][kPolyDeg + 1];    // c[j][p]: psi(f + m - 1 - j) ~ sum_p c z^p, z = 2f - 1 (FP32)
+    double c64[8][kPolyDeg64 + 1];// the same for j < m in FP64 (degree 13, error ~1e-14)
+    double beta;                  // Kaiser-Bessel shape pi (2 - 1/oversampling)
+    double scale;                 // m / sinh(beta m): normalises psi(0) to 1
 };
 
 // The 2M window weights of one coordinate with fractional cell offset f in [0, 1):
@@ -46,23 +47,19 @@ struct Weights<float, M> {
 template <int M>
 struct Weights<double, M> {
     static __device__ __forceinline__ void eval(double f, const WinParams &wp, double *w) {
+        static_assert(kPolyDeg64 % 2 == 1, "even/odd split assumes an odd degree");
+        const double z = fma(2.0, f, -1.0);
+        const double z2 = z * z;
 #pragma unroll
-        for (int j = 0; j < 2 * M; ++j) {
-            const double t = f + (double)(M - 1 - j);
-            const double s2 = (double)(M * M) - t * t;
-            double val;
-            if (s2 <= 0.0) {
-                val = (s2 == 0.0) ? wp.beta * wp.scale : 0.0;
-            } else {
-                const double s = sqrt(s2);
-                if (s < 1e-4) {
-                    const double bs2 = wp.beta * wp.beta * s2;
-                    val = wp.beta * (1.0 + bs2 * (1.0 / 6.0) + bs2 * bs2 * (1.0 / 120.0)) * wp.scale;
-                } else {
-                    val = sinh(wp.beta * s) / s * wp.scale;
-                }
+        for (int j = 0; j < M; ++j) {
+            double e = wp.c64[j][kPolyDeg64 - 1], o = wp.c64[j][kPolyDeg64];
+#pragma unroll
+            for (int p = kPolyDeg64 - 3; p >= 0; p -= 2) {
+                e = fma(e, z2, wp.c64[j][p]);
+                o = fma(o, z2, wp.c64[j][p + 1]);
             }
-            w[j] = val;
+            w[j] = fma(z, o, e);
+            w[2 * M - 1 - j] = fma(-z, o, e);
         }
     }
 };

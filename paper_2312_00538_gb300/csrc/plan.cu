@@ -317,7 +317,8 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     }
 
     // ------------------------------------------------------------------ host constants
-    if (!window_poly(m, kPolyDeg, p->poly)) return fail(ANOVA_ERR_INVALID_ARG, "window polynomial fit failed");
+    if (!window_poly(m, kPolyDeg, p->poly) || !window_poly(m, kPolyDeg64, p->poly64))
+        return fail(ANOVA_ERR_INVALID_ARG, "window polynomial fit failed");
     const int lb = ilog2(nos);
     // deconvolution diagonal per window and axis, bit-reversed; eta_l scales the axis-0 copy
     std::vector<double> d1br((size_t)P * 3 * nos, 0.0);
