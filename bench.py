@@ -147,9 +147,10 @@ def run_reference(args):
     X, W, vseed = workload(n)
     from synth import matvec_vectors
     v = matvec_vectors(n, 1, vseed)[:, 0]
-    # size each step to ~4 s of CPU work so that warmup + steps end within a few minutes
+    # size each step so that warm-up + timed steps take about two minutes (at most 4 s a step)
     rate0, rows0, _, cores = oracle_rows_per_s(X, W, args.sigma, v, 1.0, 20000, 7)
-    rows = int(max(16, min(20000, 4.0 * rate0)))
+    per_step_s = min(4.0, 120.0 / max(1, args.steps + args.warmup))
+    rows = int(max(16, min(20000, per_step_s * rate0)))
     from oracle import kernel as ok
     from synth import subsample_rows
     for i in range(args.warmup):
