@@ -9,6 +9,10 @@
 
 namespace anova {
 
+#ifndef ANOVA_SPREAD_LPP
+#define ANOVA_SPREAD_LPP 32  // lanes per point in the packed FP32 spread (16 or 32)
+#endif
+
 template <typename T>
 struct Prec;
 template <>
@@ -71,11 +75,11 @@ cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int M>
+template <int M, int LPP>
 cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
     constexpr int B = Prec<float>::B, NW = Prec<float>::SPREAD_WARPS;
-    using C = SpreadX2Cfg<M, B, NW>;
-    auto kern = k_spread3_x2<M, B, NW>;
+    using C = SpreadX2Cfg<M, B, NW, LPP>;
+    auto kern = k_spread3_x2<M, B, NW, LPP>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -132,8 +136,8 @@ template <typename T>
 cudaError_t dispatch_spread(int dw, int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         // the packed kernel reads v in sorted order; callers without that copy use the generic one
-        if (a.vsorted && dw == 3 && m == 4) return launch_spread3_x2<4>(a, nb, nrhs, st);
-        if (a.vsorted && dw == 3 && m == 2) return launch_spread3_x2<2>(a, nb, nrhs, st);
+        if (a.vsorted && dw == 3 && m == 4) return launch_spread3_x2<4, ANOVA_SPREAD_LPP>(a, nb, nrhs, st);
+        if (a.vsorted && dw == 3 && m == 2) return launch_spread3_x2<2, 16>(a, nb, nrhs, st);
     }
     switch (dw) {
         case 1: return dispatch_spread_m<T, 1>(m, a, nb, nrhs, st);

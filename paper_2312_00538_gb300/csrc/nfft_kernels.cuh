@@ -175,11 +175,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
 // points per step with fma.rn.f32x2. The staged weights are laid out so that every load is a
 // 64- or 128-bit broadcast: X duplicated into pairs and permuted so that a lane's rows are
 // contiguous, Y duplicated into pairs, Z (times v) plain.
-template <int M, int B, int NWARP>
+template <int M, int B, int NWARP, int LPP = 16>
 struct SpreadX2Cfg {
     static constexpr int W2 = 2 * M;
-    static constexpr int RPL = W2 * W2 / 16;         // rows per lane
-    static constexpr int S = 16 / W2;                // a-stride between a lane's rows
+    static constexpr int RPL = W2 * W2 / LPP;        // rows per lane (LPP lanes share a point)
+    static constexpr int S = LPP / W2;               // a-stride between a lane's rows
     static constexpr int TW = B + W2 - 1;
     static constexpr int TV = TW * TW * TW;
     static constexpr int TVP = (TV + 3) / 4 * 4;
@@ -187,12 +187,13 @@ struct SpreadX2Cfg {
     static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS);
 };
 
-template <int M, int B, int NWARP>
+template <int M, int B, int NWARP, int LPP>
 __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
-    using C = SpreadX2Cfg<M, B, NWARP>;
+    using C = SpreadX2Cfg<M, B, NWARP, LPP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
-    static_assert(16 % W2 == 0 && RPL * 16 == W2 * W2, "2M must divide 16");
-    static_assert(W2 % 4 == 0 && (RPL % 2 == 0 || RPL == 1), "vector staging layout");
+    constexpr int PPS = 32 / LPP;  // points per warp step
+    static_assert(LPP % W2 == 0 && RPL * LPP == W2 * W2, "2M must divide the lanes per point");
+    static_assert(W2 % 4 == 0, "vector staging layout");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tiles_s = reinterpret_cast<float *>(smem_raw);
     float *wts_s = tiles_s + NWARP * C::TVP;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
     if (wi_idx >= a.wi_end) return;
     const int r = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = lane >> 4, lh = lane & 15;
+    const int half = lane / LPP, lh = lane % LPP;
     const int4 wi = a.wis[wi_idx];
     const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
 
@@ -303,10 +304,10 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
                 for (int c = 0; c < W2; c += 4) dst[(C::ZO + c) / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
             }
             __syncwarp();
-            const int npair = (cnt + 1) >> 1;
+            const int nstep = (cnt + PPS - 1) / PPS;
 #pragma unroll 2
-            for (int jj = 0; jj < npair; ++jj) {
-                const float *pw = wts + (2 * jj + half) * PS;
+            for (int jj = 0; jj < nstep; ++jj) {
+                const float *pw = wts + (PPS * jj + half) * PS;
                 float xr[RPL];
                 f32x2 z2[W2 / 2];
                 const float yb = pw[C::YO + rb];
@@ -319,6 +320,10 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
                         xr[k + 2] = t.z;
                         xr[k + 3] = t.w;
                     }
+                } else if constexpr (RPL == 2) {
+                    const float2 t = *reinterpret_cast<const float2 *>(pw + C::XO + g * RPL);
+                    xr[0] = t.x;
+                    xr[1] = t.y;
                 } else {
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) xr[k] = pw[C::XO + g * RPL + k];
@@ -340,15 +345,17 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
                 int lc[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;
+                if constexpr (PPS == 2) {
 #pragma unroll
-                for (int k = 0; k < RPL; ++k)
+                    for (int k = 0; k < RPL; ++k)
 #pragma unroll
-                    for (int c = 0; c < W2 / 2; ++c) {
-                        f32x2 o;
-                        o.x = __shfl_down_sync(0xffffffffu, acc[k][c].x, 16);
-                        o.y = __shfl_down_sync(0xffffffffu, acc[k][c].y, 16);
-                        acc[k][c] = add2(acc[k][c], o);
-                    }
+                        for (int c = 0; c < W2 / 2; ++c) {
+                            f32x2 o;
+                            o.x = __shfl_down_sync(0xffffffffu, acc[k][c].x, 16);
+                            o.y = __shfl_down_sync(0xffffffffu, acc[k][c].y, 16);
+                            acc[k][c] = add2(acc[k][c], o);
+                        }
+                }
                 if (half == 0) {
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
