@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch"],
+                    help="matvec (default, the headline line) or ipm_batch (independent SVM "
+                         "solves, one at a time vs concurrently)")
+    ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
+    ap.add_argument("--concurrency", type=int, default=8, help="ipm_batch: concurrent solves")
+    ap.add_argument("--n-max", type=int, default=200_000, help="ipm_batch: largest n")
     return ap.parse_args()
 
 
@@ -347,10 +353,57 @@ def run_ours(args):
     return 0
 
 
+def run_ipm_batch(args):
+    """Independent SVM solves of workload 4 (n log-uniform, (C, sigma) grid, rank 100): the plain
+    path solves them one after another, the batched path `concurrency` at a time on separate
+    streams. Solves/s and the per-solve latency distribution of both; equal results asserted."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import config4
+    probs = config4(count=args.count, n_hi=args.n_max)
+    o = ab.svm_opts_default()
+    o.rank = 100
+    o.max_iter = 100
+    tol = 1e-6
+    plist = [dict(X=p["X"], y=p["y"], C=p["C"], ell=p["sigma"], windows=p["windows"]) for p in probs]
+    torch.cuda.synchronize()
+    ab.svm_ipm_solve_batch(plist[:2], tol, opts=o, concurrency=1)      # warm-up
+    res = {}
+    for mode, conc in (("plain", 1), ("batched", args.concurrency)):
+        t0 = time.perf_counter()
+        out = ab.svm_ipm_solve_batch(plist, tol, opts=o, concurrency=conc)
+        wall = time.perf_counter() - t0
+        lat = np.array([r[2]["time_ms"] for r in out])
+        if mode == "plain":
+            per = [dict(n=int(p["X"].shape[0]), C=p["C"], sigma=p["sigma"], it=r[2]["iterations"],
+                        krylov=r[2]["krylov_iterations"], fp64_krylov=r[2]["fp64_krylov_iterations"],
+                        rank=r[2]["rank"], ms=round(r[2]["time_ms"], 1), conv=r[2]["converged"])
+                   for p, r in zip(probs, out)]
+            print(json.dumps({"per_problem_plain": per}), file=sys.stderr, flush=True)
+        res[mode] = {"solves_per_s": len(plist) / wall, "wall_s": wall,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "converged": int(sum(r[2]["converged"] for r in out)),
+                     "alphas": [r[0] for r in out]}
+    same = all(np.array_equal(a, b) for a, b in zip(res["plain"].pop("alphas"), res["batched"].pop("alphas")))
+    line = {"metric": "IPM solves/s (workload 4, batched vs plain)", "value": res["batched"]["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "%d SVM problems, n log-uniform [5e3, %d], d=9, C x sigma grid, rank 100, "
+                                   "gap 1e-6" % (args.count, args.n_max), "concurrency": args.concurrency},
+            "plain": res["plain"], "batched": res["batched"], "results_identical": bool(same),
+            "speedup": res["batched"]["solves_per_s"] / res["plain"]["solves_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ipm_batch":
+        return run_ipm_batch(args)
     return run_ours(args)
 
 

@@ -130,6 +130,34 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *y, d
                            double tol, const svm_opts *opts, double *alpha, double *b,
                            svm_stats *stats);
 
+/* One problem of a batch (inputs as svm_ipm_solve; outputs filled by svm_ipm_solve_batch). */
+typedef struct {
+    const double *X;         /* host, n x d row-major */
+    int64_t n;
+    int d;
+    const double *y;         /* host, n labels in {-1, +1} */
+    double C;
+    double ell;              /* kernel length scale; <= 0 takes opts->ell */
+    const int32_t *windows;  /* P x 3 (-1 padded); NULL takes opts->windows / consecutive windows */
+    int P;
+    double *alpha;           /* host, n doubles (output) */
+    double b;                /* output: bias b = -lambda */
+    svm_stats stats;         /* output */
+    anova_status status;     /* output: status of this problem's solve */
+} svm_problem;
+
+/*
+ * svm_ipm_solve_batch -- solve `count` independent problems, `concurrency` at a time: each of
+ * `concurrency` host workers owns a CUDA stream of the current device and solves its share of
+ * the problems one after another on it, so the small kernels and host round trips of several
+ * solves overlap on the GPU. Every problem is solved exactly as svm_ipm_solve would solve it
+ * alone with the same opts (opts->cuda_stream is replaced by the worker's stream), so each result
+ * is bitwise the same alone and in the batch. Returns ANOVA_OK if every problem succeeded,
+ * otherwise the first failing problem's status (each problem carries its own status).
+ */
+anova_status svm_ipm_solve_batch(svm_problem *problems, int count, double tol,
+                                 const svm_opts *opts, int concurrency);
+
 #ifdef __cplusplus
 }
 #endif

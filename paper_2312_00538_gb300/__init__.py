@@ -75,6 +75,7 @@ _SIGNATURES = {
     "lowrank_destroy": (None, [_vp]),
     "svm_opts_default": (None, [_vp]),
     "svm_ipm_solve": (_c_int, [_dp, _c_i64, _c_int, _dp, _c_dbl, _c_dbl, _vp, _dp, _dp, _vp]),
+    "svm_ipm_solve_batch": (_c_int, [_vp, _c_int, _c_dbl, _vp, _c_int]),
     "anova_last_error": (ctypes.c_char_p, []),
     "anova_version": (ctypes.c_char_p, []),
 }
@@ -397,3 +398,49 @@ def svm_ipm_solve(X, y, C, tol, opts=None, windows=None):
         _check(status)
     del keep
     return alpha, b.value, st.as_dict(), status
+
+
+class svm_problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.POINTER(ctypes.c_double)), ("n", ctypes.c_int64), ("d", ctypes.c_int),
+                ("y", ctypes.POINTER(ctypes.c_double)), ("C", ctypes.c_double), ("ell", ctypes.c_double),
+                ("windows", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.c_double),
+                ("stats", svm_stats), ("status", ctypes.c_int)]
+
+
+def svm_ipm_solve_batch(problems, tol, opts=None, concurrency=8):
+    """svm_ipm_solve_batch over a list of dicts with keys X, y, C and optionally ell, windows.
+
+    Returns a list of (alpha, b, stats dict, status) in the input order."""
+    keep = []
+    arr = (svm_problem * len(problems))()
+    alphas = []
+    for i, pr in enumerate(problems):
+        X = _f64(pr["X"])
+        y = _f64(pr["y"])
+        al = np.zeros(X.shape[0])
+        keep += [X, y]
+        alphas.append(al)
+        arr[i].X = _ptr(X, ctypes.c_double)
+        arr[i].n = X.shape[0]
+        arr[i].d = X.shape[1]
+        arr[i].y = _ptr(y, ctypes.c_double)
+        arr[i].C = float(pr["C"])
+        arr[i].ell = float(pr.get("ell", 0.0))
+        if pr.get("windows") is not None:
+            W = np.ascontiguousarray(pr["windows"], dtype=np.int32).reshape(-1, 3)
+            keep.append(W)
+            arr[i].windows = _ptr(W, ctypes.c_int32)
+            arr[i].P = W.shape[0]
+        arr[i].alpha = _ptr(al, ctypes.c_double)
+    o = opts if opts is not None else svm_opts_default()
+    lib().svm_ipm_solve_batch(ctypes.byref(arr), len(problems), float(tol), ctypes.byref(o),
+                              int(concurrency))
+    out = []
+    for i in range(len(problems)):
+        st = arr[i].status
+        if st not in (ANOVA_OK, ANOVA_ERR_NOT_CONVERGED):
+            raise AnovaError(st, "problem %d of the batch failed" % i)
+        out.append((alphas[i], arr[i].b, arr[i].stats.as_dict(), st))
+    del keep
+    return out

@@ -187,6 +187,9 @@ __global__ void k_core_sum(const double *__restrict__ part, int nchunks, int nti
         const int aa = e >> 5, bb = e & 31;
         const int a = t.x * 32 + aa, b = t.y * 32 + bb;
         if (a >= r || b >= r) continue;
+        // one thread writes both mirrored entries (in a diagonal tile only the lower half works),
+        // so M does not depend on which of two slightly different sums lands last
+        if (t.x == t.y && bb > aa) continue;
         double s = 0.0;
         for (int c = 0; c < nchunks; ++c) s += part[(((long long)c * ntiles + tile) * 32 + aa) * 32 + bb];
         if (a == b) s += 1.0;
@@ -223,27 +226,74 @@ __global__ void __launch_bounds__(1024) k_cholesky(double *M, int r, int *info) 
     if (threadIdx.x == 0) *info = bad;
 }
 
-// Solve (R R^T) z = u with the lower factor R (row-major), one CTA, in place in z.
-__global__ void __launch_bounds__(1024) k_chol_solve(const double *__restrict__ R, int r, double *z) {
-    for (int k = 0; k < r; ++k) {  // forward: R w = u
-        __syncthreads();
-        if (threadIdx.x == 0) z[k] /= R[(long long)k * r + k];
-        __syncthreads();
-        const double zk = z[k];
-        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) z[i] -= R[(long long)i * r + k] * zk;
+// Solve (R R^T) z = u for the lower Cholesky factor R (row-major): the CTA stages R's lower
+// triangle in shared memory (r <= kSmemCholMax; otherwise it is read from global memory), then
+// one warp runs the forward and backward substitutions with warp-level synchronisation only.
+__global__ void __launch_bounds__(256) k_chol_solve_warp(const double *__restrict__ R, int r, const double *__restrict__ u,
+                                                          double *__restrict__ z) {
+    extern __shared__ double sm[];
+    const bool in_smem = r <= 160;
+    double *zs = sm;
+    double *Rs = sm + r;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) zs[i] = u[i];
+    if (in_smem)
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[e];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const double *A = in_smem ? Rs : R;
+    const int lane = threadIdx.x;
+    for (int k = 0; k < r; ++k) {  // R w = u
+        const double zk = zs[k] / A[(long long)k * r + k];
+        __syncwarp();
+        if (lane == 0) zs[k] = zk;
+        for (int i = k + 1 + lane; i < r; i += 32) zs[i] -= A[(long long)i * r + k] * zk;
+        __syncwarp();
     }
-    for (int k = r - 1; k >= 0; --k) {  // backward: R^T z = w
-        __syncthreads();
-        if (threadIdx.x == 0) z[k] /= R[(long long)k * r + k];
-        __syncthreads();
-        const double zk = z[k];
-        for (int i = threadIdx.x; i < k; i += blockDim.x) z[i] -= R[(long long)k * r + i] * zk;
+    for (int k = r - 1; k >= 0; --k) {  // R^T z = w
+        const double zk = zs[k] / A[(long long)k * r + k];
+        __syncwarp();
+        if (lane == 0) zs[k] = zk;
+        for (int i = lane; i < k; i += 32) zs[i] -= A[(long long)k * r + i] * zk;
+        __syncwarp();
     }
+    for (int i = lane; i < r; i += 32) z[i] = zs[i];
 }
 
-// u_part[c](q) = sum_{i in chunk c} L(i, q) t_i with t = y .* g ./ theta; one warp per column,
-// lanes over the chunk's rows.
-constexpr int kApplyRows = 8192;
+// In-place Cholesky as k_cholesky, with the matrix staged in shared memory (r <= kSmemCholMax).
+constexpr int kSmemCholMax = 160;
+
+__global__ void __launch_bounds__(1024) k_cholesky_smem(double *M, int r, int *info) {
+    extern __shared__ double A[];
+    __shared__ double piv;
+    __shared__ int bad;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) A[e] = M[e];
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            const double dk = A[k * r + k];
+            if (!(dk > 0.0)) bad = k + 1;
+            piv = sqrt(dk > 0.0 ? dk : 1.0);
+            A[k * r + k] = piv;
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + k] /= piv;
+        __syncthreads();
+        const int m = r - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, jj = k + 1 + e % m;
+            if (jj <= i) A[i * r + jj] -= A[i * r + k] * A[jj * r + k];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) M[e] = A[e];
+    if (threadIdx.x == 0) *info = bad;
+}
+
+// u_part[c](q) = sum_{i in chunk c} L(i, q) t_i with t = y .* g ./ theta. Grid: (row chunks,
+// groups of 8 columns); one warp per column, lanes over the chunk's rows.
+constexpr int kApplyRows = 1024;
 
 __global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, const double *__restrict__ theta,
                                                  const double *__restrict__ y, const double *__restrict__ g,
@@ -251,13 +301,13 @@ __global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, co
     const long long i0 = (long long)blockIdx.x * kApplyRows;
     const long long i1 = min(n, i0 + kApplyRows);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = warp; q < r; q += blockDim.x >> 5) {
-        const float *col = L + (long long)q * n;
-        double s = 0.0;
-        for (long long i = i0 + lane; i < i1; i += 32) s += (double)col[i] * (y[i] * g[i] / theta[i]);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) upart[(long long)blockIdx.x * r + q] = s;
-    }
+    const int q = blockIdx.y * 8 + warp;
+    if (q >= r) return;
+    const float *col = L + (long long)q * n;
+    double s = 0.0;
+    for (long long i = i0 + lane; i < i1; i += 32) s += (double)col[i] * (y[i] * g[i] / theta[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) upart[(long long)blockIdx.x * r + q] = s;
 }
 
 __global__ void k_panel_t_sum(const double *__restrict__ upart, int nchunks, int r, double *__restrict__ u) {
@@ -387,7 +437,8 @@ int grid_for(long long n, int threads, int cap = 152 * 8) {
 void lowrank_release(lowrank *lr) {
     if (!lr) return;
     void *bufs[] = {lr->L64, lr->L32, lr->d, lr->piv_dev, lr->dpiv, lr->stop, lr->partial, lr->M,
-                    lr->u, lr->upart, lr->tiles, lr->cpart, lr->info, lr->tmp, lr->dpart, lr->schur};
+                    lr->u, lr->z, lr->upart, lr->tiles, lr->cpart, lr->info, lr->tmp,
+                    lr->dpart, lr->schur};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete lr;
@@ -481,6 +532,8 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
     lr->napply = (int)((n + kApplyRows - 1) / kApplyRows);
     if ((e = cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
         (e = cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
+        (e = cudaMalloc(&lr->z, sizeof(double) * rank)) != cudaSuccess ||
+
         (e = cudaMalloc(&lr->upart, sizeof(double) * rank * lr->napply)) != cudaSuccess ||
         (e = cudaMalloc(&lr->tiles, sizeof(int2) * tiles.size())) != cudaSuccess ||
         (e = cudaMalloc(&lr->cpart, sizeof(double) * 1024 * tiles.size() * lr->nchunks)) != cudaSuccess ||
@@ -502,10 +555,16 @@ anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, c
     cudaStream_t st = p->stream;
     const long long n = lr->n;
     const int r = lr->rank;
-    k_panel_t<<<lr->napply, 256, 0, st>>>(lr->L32, theta, y, g, n, r, lr->upart);
+    k_panel_t<<<dim3(lr->napply, (r + 7) / 8), 256, 0, st>>>(lr->L32, theta, y, g, n, r, lr->upart);
     k_panel_t_sum<<<grid_for(r, 128), 128, 0, st>>>(lr->upart, lr->napply, r, lr->u);
-    k_chol_solve<<<1, 1024, 0, st>>>(lr->M, r, lr->u);
-    k_panel_n<<<grid_for(n, 256, 152 * 8), 256, sizeof(double) * r, st>>>(lr->L32, theta, y, g, lr->u, n, r, x,
+    {
+        const size_t shm = sizeof(double) * (r + (r <= 160 ? (size_t)r * r : 0));
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            k_chol_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * (160 + 160 * 160)));
+        if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute");
+        k_chol_solve_warp<<<1, 256, shm, st>>>(lr->M, r, lr->u, lr->z);   // z = M^{-1} u
+    }
+    k_panel_n<<<grid_for(n, 256, 152 * 8), 256, sizeof(double) * r, st>>>(lr->L32, theta, y, g, lr->z, n, r, x,
                                                                           with_schur ? lr->schur : nullptr);
     ANOVA_CUDA_TRY(cudaGetLastError());
     return ANOVA_OK;
@@ -519,7 +578,14 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
     k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, theta, n, r, (const int2 *)lr->tiles,
                                                                    lr->cpart);
     k_core_sum<<<lr->ntiles, 256, 0, st>>>(lr->cpart, lr->nchunks, lr->ntiles, (const int2 *)lr->tiles, r, lr->M);
-    k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info);
+    if (r <= kSmemCholMax) {
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * kSmemCholMax * kSmemCholMax));
+        if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute");
+        k_cholesky_smem<<<1, 1024, sizeof(double) * r * r, st>>>(lr->M, r, lr->info);
+    } else {
+        k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info);
+    }
     ANOVA_CUDA_TRY(cudaGetLastError());
     int info = 0;
     ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));

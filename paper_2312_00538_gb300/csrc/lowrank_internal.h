@@ -19,7 +19,7 @@ struct lowrank {
     void *partial = nullptr;
     // Woodbury core
     double *M = nullptr;         // rank x rank, Cholesky factor after set_theta
-    double *u = nullptr, *upart = nullptr;
+    double *u = nullptr, *upart = nullptr, *z = nullptr;
     void *tiles = nullptr;
     double *cpart = nullptr;
     int *info = nullptr;

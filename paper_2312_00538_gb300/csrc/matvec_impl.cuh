@@ -33,13 +33,9 @@ cudaError_t launch_spread_t(const SpreadArgs &a, int nblocks, int nrhs, cudaStre
     constexpr int B = Prec<T>::B, NW = Prec<T>::SPREAD_WARPS;
     using C = SpreadCfg<T, DW, M, B, NW>;
     auto kern = k_spread<T, DW, M, B, NW>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -49,13 +45,9 @@ cudaError_t launch_interp_t(const InterpArgs &a, int nseg, int nrhs, cudaStream_
     constexpr int NW = Prec<T>::INTERP_WARPS;
     using C = InterpCfg<T, DW, M, NW>;
     auto kern = k_interp<T, DW, M, NW>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<dim3((nseg + NW - 1) / NW, nrhs), NW * 32, C::smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -64,13 +56,9 @@ template <typename T, int NOS, int DW>
 cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t st) {
     using C = ConvCfg<T, NOS>;
     auto kern = k_conv<T, NOS, DW>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<dim3(ntiles, nrhs), 256, C::smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -80,13 +68,9 @@ cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaSt
     constexpr int B = Prec<float>::B, NW = Prec<float>::SPREAD_WARPS;
     using C = SpreadX2Cfg<M, B, NW, LPP>;
     auto kern = k_spread3_x2<M, B, NW, LPP>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -96,15 +80,78 @@ cudaError_t launch_interp3_x2(const InterpWiArgs &a, int nblocks, int nrhs, cuda
     constexpr int B = Prec<float>::B, NW = Prec<float>::INTERP_WARPS;
     using C = InterpX2Cfg<M, B, NW>;
     auto kern = k_interp3_x2<M, B, NW>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int DW, int M>
+cudaError_t launch_interp_bin_t(const InterpBinArgs<T> &a, int nblocks, int nrhs, cudaStream_t st) {
+    constexpr int B = Prec<T>::B, NW = 4;
+    using C = InterpBinCfg<T, DW, M, B, NW>;
+    auto kern = k_interp_bin<T, DW, M, B, NW>;
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
+    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int DW>
+cudaError_t dispatch_interp_bin_m(int m, const InterpBinArgs<T> &a, int nb, int nrhs, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        switch (m) {
+            case 2: return launch_interp_bin_t<T, DW, 2>(a, nb, nrhs, st);
+            case 3: return launch_interp_bin_t<T, DW, 3>(a, nb, nrhs, st);
+            case 4: return launch_interp_bin_t<T, DW, 4>(a, nb, nrhs, st);
+            case 5: return launch_interp_bin_t<T, DW, 5>(a, nb, nrhs, st);
+            case 6: return launch_interp_bin_t<T, DW, 6>(a, nb, nrhs, st);
+        }
+    } else {
+        switch (m) {
+            case 3: return launch_interp_bin_t<T, DW, 3>(a, nb, nrhs, st);
+            case 4: return launch_interp_bin_t<T, DW, 4>(a, nb, nrhs, st);
+            case 5: return launch_interp_bin_t<T, DW, 5>(a, nb, nrhs, st);
+            case 6: return launch_interp_bin_t<T, DW, 6>(a, nb, nrhs, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t dispatch_interp_bin(int dw, int m, const InterpBinArgs<T> &a, int nb, int nrhs, cudaStream_t st) {
+    switch (dw) {
+        case 1: return dispatch_interp_bin_m<T, 1>(m, a, nb, nrhs, st);
+        case 2: return dispatch_interp_bin_m<T, 2>(m, a, nb, nrhs, st);
+        case 3: return dispatch_interp_bin_m<T, 3>(m, a, nb, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int DW>
+cudaError_t dispatch_interp_direct_m(int m, const InterpDirectArgs<T> &a, int nrhs, cudaStream_t st) {
+    const long long cnt = a.q_end - a.q_begin;
+    const dim3 grid((unsigned)((cnt + 127) / 128), nrhs);
+    switch (m) {
+        case 3: k_interp_direct<T, DW, 3><<<grid, 128, 0, st>>>(a); break;
+        case 4: k_interp_direct<T, DW, 4><<<grid, 128, 0, st>>>(a); break;
+        case 5: k_interp_direct<T, DW, 5><<<grid, 128, 0, st>>>(a); break;
+        case 6: k_interp_direct<T, DW, 6><<<grid, 128, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_interp_direct(int dw, int m, const InterpDirectArgs<T> &a, int nrhs, cudaStream_t st) {
+    switch (dw) {
+        case 1: return dispatch_interp_direct_m<T, 1>(m, a, nrhs, st);
+        case 2: return dispatch_interp_direct_m<T, 2>(m, a, nrhs, st);
+        case 3: return dispatch_interp_direct_m<T, 3>(m, a, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 // the FP32 3-D paths with a packed kernel (footprint edge 2m divides 16)
@@ -382,8 +429,48 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
                                       : launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "interp launch");
             p->launches += 1;
-        } else if (s1 > s0) {
-            cudaError_t e = dispatch_interp<T>(gr.dw, p->m, ia, s1 - s0, nrhs, st);
+        } else if (sizeof(T) == 8 && s1 > s0) {
+            InterpDirectArgs<T> da;
+            da.frac = reinterpret_cast<const T *>(p->frac);
+            da.perm = p->perm;
+            da.segs = p->segs;
+            da.grid = g[3];
+            da.dwin = p->dwin;
+            da.part = part;
+            da.n = p->n;
+            da.total = p->n * p->P;
+            da.grid_stride_rhs = grid_stride;
+            da.nrhs = nrhs;
+            da.seg_begin = s0;
+            da.seg_end = s1;
+            da.n_os = p->n_os;
+            da.part_w0 = w0;
+            da.q_begin = (long long)a0 * p->n;
+            da.q_end = (long long)a1 * p->n;
+            da.wp = wp;
+            cudaError_t e = dispatch_interp_direct<T>(gr.dw, p->m, da, nrhs, st);
+            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+            p->launches += 1;
+        } else if (wi1 > wi0) {
+            InterpBinArgs<T> ba;
+            ba.wis = p->wis;
+            ba.segs = p->segs;
+            ba.frac = reinterpret_cast<const T *>(p->frac);
+            ba.perm = p->perm;
+            ba.cellloc = p->cellloc;
+            ba.grid = g[3];
+            ba.dwin = p->dwin;
+            ba.part = part;
+            ba.n = p->n;
+            ba.total = p->n * p->P;
+            ba.grid_stride_rhs = grid_stride;
+            ba.nrhs = nrhs;
+            ba.wi_begin = wi0;
+            ba.wi_end = wi1;
+            ba.n_os = p->n_os;
+            ba.part_w0 = w0;
+            ba.wp = wp;
+            cudaError_t e = dispatch_interp_bin<T>(gr.dw, p->m, ba, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "interp launch");
             p->launches += 1;
         }

@@ -764,6 +764,189 @@ __global__ void __launch_bounds__(NWARP * 32) k_interp3_x2(InterpWiArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ interpolation, any dims
+// The general form of the per-bin interpolation (any precision, 1-3 dims, any cut-off): one CTA
+// per work item stages the bin's grid neighbourhood ((B + 2M - 1)^d values) in shared memory,
+// warps split the item's points evenly, one point per lane, scalar shared-memory reads.
+template <typename T>
+struct InterpBinArgs {
+    const int4 *wis;
+    const int4 *segs;
+    const T *frac;
+    const int *perm;
+    const unsigned char *cellloc;
+    const T *grid;
+    const DevWindow *dwin;
+    T *part;
+    long long n, total, grid_stride_rhs;
+    int nrhs, wi_begin, wi_end, n_os, part_w0;
+    WinParams wp;
+};
+
+template <typename T, int DW, int M, int B, int NWARP>
+struct InterpBinCfg {
+    static constexpr int W2 = 2 * M;
+    static constexpr int TW = B + W2 - 1;
+    static constexpr int TV = ipow(TW, DW);
+    static constexpr size_t smem = sizeof(T) * (size_t)TV;
+};
+
+template <typename T, int DW, int M, int B, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32) k_interp_bin(InterpBinArgs<T> a) {
+    using C = InterpBinCfg<T, DW, M, B, NWARP>;
+    constexpr int W2 = C::W2, TW = C::TW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bt = reinterpret_cast<T *>(smem_raw);
+    const int wi_idx = a.wi_begin + blockIdx.x;
+    if (wi_idx >= a.wi_end) return;
+    const int r = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 wi = a.wis[wi_idx];
+    const int w = wi.x;
+    const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
+    const DevWindow dw = a.dwin[w];
+    const T *grid = a.grid + (size_t)r * a.grid_stride_rhs + dw.grid_off;
+    for (int e = threadIdx.x; e < C::TV; e += NWARP * 32) {
+        int rem = e;
+        long long g = 0;
+        int l[3] = {0, 0, 0};
+        for (int k = DW - 1; k >= 0; --k) {
+            l[k] = rem % TW;
+            rem /= TW;
+        }
+        for (int k = 0; k < DW; ++k) g = g * a.n_os + (bin[k] * B - M + 1 + l[k]);
+        bt[e] = grid[g];
+    }
+    __syncthreads();
+    const int4 s_first = a.segs[wi.y];
+    const int4 s_last = a.segs[wi.z - 1];
+    const int p0 = s_first.y, p1 = s_last.y + s_last.z;
+    const int len = p1 - p0;
+    const int pw0 = p0 + (int)(((long long)len * warp) / NWARP);
+    const int pw1 = p0 + (int)(((long long)len * (warp + 1)) / NWARP);
+    T *out = a.part + ((size_t)(w - a.part_w0) * a.nrhs + r) * a.n;
+    for (int qb = pw0; qb < pw1; qb += 32) {
+        const bool valid = qb + lane < pw1;
+        const int q = qb + min(lane, pw1 - qb - 1);
+        int loc = a.cellloc[q];
+        int lc[3] = {0, 0, 0};
+        for (int k = DW - 1; k >= 0; --k) {
+            lc[k] = loc % B;
+            loc /= B;
+        }
+        T wt[DW][W2];
+#pragma unroll
+        for (int k = 0; k < DW; ++k) Weights<T, M>::eval(a.frac[(size_t)k * a.total + q], a.wp, wt[k]);
+        T f = T(0);
+        if (DW == 3) {
+#pragma unroll 1
+            for (int aa = 0; aa < W2; ++aa) {
+                T sa = T(0);
+                for (int bb = 0; bb < W2; ++bb) {
+                    const T *row = bt + ((lc[0] + aa) * TW + (lc[1] + bb)) * TW + lc[2];
+                    T sb = T(0);
+#pragma unroll
+                    for (int cc = 0; cc < W2; ++cc) sb = fma(row[cc], wt[2][cc], sb);
+                    sa = fma(wt[1][bb], sb, sa);
+                }
+                T wxa = wt[0][0];
+#pragma unroll
+                for (int k = 1; k < W2; ++k)
+                    if (k == aa) wxa = wt[0][k];
+                f = fma(wxa, sa, f);
+            }
+        } else if (DW == 2) {
+#pragma unroll
+            for (int aa = 0; aa < W2; ++aa) {
+                const T *row = bt + (lc[0] + aa) * TW + lc[1];
+                T sb = T(0);
+#pragma unroll
+                for (int cc = 0; cc < W2; ++cc) sb = fma(row[cc], wt[1][cc], sb);
+                f = fma(wt[0][aa], sb, f);
+            }
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < W2; ++cc) f = fma(bt[lc[0] + cc], wt[0][cc], f);
+        }
+        if (valid) out[a.perm[q]] = f;
+    }
+}
+
+// ------------------------------------------------------------------ interpolation, direct reads
+// One thread per point reading its (2M)^d grid block straight from the (L2-resident) grid. Used
+// where staging a bin's neighbourhood costs more than it saves: the FP64 plan, whose bins hold
+// few points (n_os = 128, B = 2) and whose FMA rate is low.
+template <typename T>
+struct InterpDirectArgs {
+    const T *frac;
+    const int *perm;
+    const int4 *segs;
+    const T *grid;
+    const DevWindow *dwin;
+    T *part;
+    long long n, total, grid_stride_rhs;
+    int nrhs, seg_begin, seg_end, n_os, part_w0;
+    long long q_begin, q_end;  // sorted points of the windows handled
+    WinParams wp;
+};
+
+template <typename T, int DW, int M>
+__global__ void __launch_bounds__(128) k_interp_direct(InterpDirectArgs<T> a) {
+    constexpr int W2 = 2 * M;
+    const int r = blockIdx.y;
+    const long long q = a.q_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.q_end) return;
+    // the segment holding q gives its cell and window (binary search over segment starts)
+    int lo = a.seg_begin, hi = a.seg_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].y <= q) lo = mid; else hi = mid - 1;
+    }
+    const int4 sg = a.segs[lo];
+    const int w = sg.w;
+    const DevWindow dw = a.dwin[w];
+    const T *grid = a.grid + (size_t)r * a.grid_stride_rhs + dw.grid_off;
+    int c0[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c0[k] = cell_coord(sg.x, k) - M + 1;
+    T wt[DW][W2];
+#pragma unroll
+    for (int k = 0; k < DW; ++k) Weights<T, M>::eval(a.frac[(size_t)k * a.total + q], a.wp, wt[k]);
+    T f = T(0);
+    if (DW == 3) {
+        const long long n2 = (long long)a.n_os * a.n_os;
+#pragma unroll 1
+        for (int aa = 0; aa < W2; ++aa) {
+            T sa = T(0);
+            for (int bb = 0; bb < W2; ++bb) {
+                const T *row = grid + (long long)(c0[0] + aa) * n2 + (long long)(c0[1] + bb) * a.n_os + c0[2];
+                T sb = T(0);
+#pragma unroll
+                for (int cc = 0; cc < W2; ++cc) sb = fma(__ldg(row + cc), wt[2][cc], sb);
+                sa = fma(wt[1][bb], sb, sa);
+            }
+            T wxa = wt[0][0];
+#pragma unroll
+            for (int k = 1; k < W2; ++k)
+                if (k == aa) wxa = wt[0][k];
+            f = fma(wxa, sa, f);
+        }
+    } else if (DW == 2) {
+#pragma unroll
+        for (int aa = 0; aa < W2; ++aa) {
+            const T *row = grid + (long long)(c0[0] + aa) * a.n_os + c0[1];
+            T sb = T(0);
+#pragma unroll
+            for (int cc = 0; cc < W2; ++cc) sb = fma(__ldg(row + cc), wt[1][cc], sb);
+            f = fma(wt[0][aa], sb, f);
+        }
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < W2; ++cc) f = fma(__ldg(grid + c0[0] + cc), wt[0][cc], f);
+    }
+    a.part[((size_t)(w - a.part_w0) * a.nrhs + r) * a.n + a.perm[q]] = f;
+}
+
 // ------------------------------------------------------------------ sum over windows
 template <typename T>
 __global__ void k_window_sum(const T *__restrict__ part, T *__restrict__ Kv, long long n, int nrhs,

@@ -5,7 +5,9 @@
 // the host adds in a fixed order, so results are reproducible). Also exports the low-rank
 // preconditioner calls of anova_svm.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -603,6 +605,56 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
     } catch (...) {
         return fail(ANOVA_ERR_INVALID_ARG, "unexpected exception");
     }
+}
+
+anova_status svm_ipm_solve_batch(svm_problem *problems, int count, double tol, const svm_opts *opts_in,
+                                 int concurrency) {
+    if (count < 0 || (count > 0 && !problems)) return fail(ANOVA_ERR_INVALID_ARG, "bad problem array");
+    if (count == 0) return ANOVA_OK;
+    svm_opts base;
+    svm_opts_default(&base);
+    if (opts_in) base = *opts_in;
+    int dev = 0;
+    ANOVA_CUDA_TRY(cudaGetDevice(&dev));
+    const int workers = std::max(1, std::min(concurrency, count));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+                problems[i].status = ANOVA_ERR_CUDA;
+            }
+            return;
+        }
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+            svm_problem &pr = problems[i];
+            svm_opts o = base;
+            o.cuda_stream = st;
+            if (pr.ell > 0) o.ell = pr.ell;
+            if (pr.windows) {
+                o.windows = pr.windows;
+                o.P = pr.P;
+            }
+            std::memset(&pr.stats, 0, sizeof(pr.stats));
+            pr.b = 0.0;
+            pr.status = svm_ipm_solve(pr.X, pr.n, pr.d, pr.y, pr.C, tol, &o, pr.alpha, &pr.b, &pr.stats);
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    if (workers == 1) {
+        worker();
+    } else {
+        std::vector<std::thread> pool;
+        pool.reserve(workers);
+        for (int t = 0; t < workers; ++t) pool.emplace_back(worker);
+        for (auto &t : pool) t.join();
+    }
+    for (int i = 0; i < count; ++i)
+        if (problems[i].status != ANOVA_OK)
+            return fail(problems[i].status, "problem " + std::to_string(i) + " of the batch failed");
+    return ANOVA_OK;
 }
 
 }  // extern "C"

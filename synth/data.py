@@ -113,3 +113,27 @@ def subsample_rows(n, k, seed):
     """k distinct row indices of [0, n), sorted."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
+
+
+C_GRID = (0.1, 1.0, 10.0, 100.0)
+SIGMA_GRID = (0.5, 1.0, 2.0, 4.0)
+
+
+def config4(count=64, n_lo=5_000, n_hi=200_000, seed=None, d=9):
+    """Workload 4: `count` independent problems, n log-uniform in [n_lo, n_hi], d = 9 (three 3-D
+    windows), labels from the tanh teacher with 5 % flips, (C, sigma) = grid[i mod 16] of
+    C in {0.1, 1, 10, 100} x sigma in {0.5, 1, 2, 4}."""
+    rng = np.random.default_rng(SEED_BASE + 4 if seed is None else seed)
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=count)).astype(np.int64)
+    probs = []
+    for i in range(count):
+        sub = np.random.default_rng(SEED_BASE + 4000 + i)
+        n = int(ns[i])
+        Xr = sub.standard_normal((n, d))
+        y = _sign(_tanh_teacher(sub, Xr))
+        flip = sub.choice(n, size=int(round(0.05 * n)), replace=False)
+        y[flip] = -y[flip]
+        g = i % 16
+        probs.append(dict(X=minmax_scale(Xr), y=y, windows=consecutive_windows(d),
+                          C=C_GRID[g // 4], sigma=SIGMA_GRID[g % 4]))
+    return probs
