@@ -42,12 +42,15 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve"],
                     help="matvec (default, the headline line) or ipm_batch (independent SVM "
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
     ap.add_argument("--concurrency", type=int, default=8, help="ipm_batch: concurrent solves")
-    ap.add_argument("--n-max", type=int, default=200_000, help="ipm_batch: largest n")
+    ap.add_argument("--n-max", type=int, default=200_000, help="ipm_batch/serve: largest n")
+    ap.add_argument("--rate", type=float, default=1.0,
+                    help="serve: mean arrival rate of requests (Poisson, requests/s)")
+    ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: device-memory budget")
     return ap.parse_args()
 
 
@@ -398,12 +401,70 @@ def run_ipm_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving loop over workload-4 problems: requests arrive as a seeded Poisson stream at
+    `rate` per second and are admitted by the native server (free slot + device-memory budget).
+    Reports throughput and the latency (arrival to completion) distribution."""
+    import threading
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import config4
+    probs = config4(count=args.count, n_hi=args.n_max)
+    o = ab.svm_opts_default()
+    o.rank = 100
+    o.max_iter = 100
+    tol = 1e-6
+    torch.cuda.synchronize()
+    ab.svm_ipm_solve_batch([dict(X=p["X"], y=p["y"], C=p["C"], ell=p["sigma"], windows=p["windows"])
+                            for p in probs[:2]], tol, opts=o, concurrency=1)      # warm-up
+    gaps = np.random.default_rng(20231201).exponential(1.0 / args.rate, size=len(probs))
+    srv = ab.SvmServer(tol, opts=o, slots=args.concurrency,
+                       hbm_budget_bytes=int(args.budget_gib * (1 << 30)))
+    tickets = []
+
+    def producer():
+        t_next = time.perf_counter()
+        for p, g in zip(probs, gaps):
+            t_next += g
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(p["X"], p["y"], p["C"], ell=p["sigma"], windows=p["windows"]))
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    srv.drain()
+    wall = time.perf_counter() - t0
+    outs = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.destroy()
+    line = {"metric": "SVM serving: solves/s at Poisson arrivals (workload 4)",
+            "value": len(probs) / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "%d SVM problems, n log-uniform [5e3, %d], d=9, C x sigma grid, rank 100, "
+                                   "gap 1e-6" % (args.count, args.n_max),
+                       "arrival_rate_per_s": args.rate, "slots": args.concurrency,
+                       "budget_gib": args.budget_gib},
+            "wall_s": wall, "p50_latency_ms": st["p50_latency_ms"], "p99_latency_ms": st["p99_latency_ms"],
+            "mean_latency_ms": st["mean_latency_ms"],
+            "peak_reserved_gib": st["peak_reserved_bytes"] / (1 << 30),
+            "converged": int(sum(r[2]["converged"] for r in outs))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ipm_batch":
         return run_ipm_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

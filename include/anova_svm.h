@@ -158,6 +158,44 @@ typedef struct {
 anova_status svm_ipm_solve_batch(svm_problem *problems, int count, double tol,
                                  const svm_opts *opts, int concurrency);
 
+/*
+ * Serving: a request loop over svm_ipm_solve. The paper has no serving layer; this follows the
+ * traffic its Sec. 6 parameter search generates (many solves of different sizes and (C, ell)).
+ *
+ * svm_server_create starts `slots` workers on the current device, each with its own CUDA stream.
+ * Requests (svm_problem, whose input and output buffers must stay valid until the request
+ * completes) are queued by svm_server_submit and started in arrival order as soon as a worker is
+ * free AND the device-memory estimate of the request fits in `hbm_budget_bytes` together with the
+ * requests already running (a request larger than the whole budget runs alone). While a solve
+ * runs, its plans, grids, preconditioner and iterates stay on the device; solves on different
+ * workers overlap on the GPU. Each result is bitwise the one svm_ipm_solve gives alone with the
+ * same opts. Latency of a request = completion time - submission time.
+ */
+typedef struct svm_server *svm_server_t;
+
+typedef struct {
+    int64_t submitted, completed, running, queued;
+    int64_t reserved_bytes;       /* device-memory estimate of the running requests */
+    int64_t peak_reserved_bytes;  /* the largest reserved_bytes seen */
+    double p50_latency_ms, p99_latency_ms, mean_latency_ms;  /* over completed requests */
+} svm_server_stats;
+
+anova_status svm_server_create(const svm_opts *opts, double tol, int slots, int64_t hbm_budget_bytes,
+                               svm_server_t *out);
+/* Queue one request; returns at once. *ticket identifies it for svm_server_wait. */
+anova_status svm_server_submit(svm_server_t server, svm_problem *problem, int64_t *ticket);
+/* Block until the request completes; returns its status (also stored in problem->status). */
+anova_status svm_server_wait(svm_server_t server, int64_t ticket);
+/* Block until every submitted request has completed. */
+anova_status svm_server_drain(svm_server_t server);
+anova_status svm_server_get_stats(svm_server_t server, svm_server_stats *stats);
+/* Device-memory estimate (bytes) the server reserves for a request of n points and P windows
+ * solved with `opts` (NULL: defaults): both plans, the low-rank factor and the solver vectors.
+ * Returns 0 for n < 1 or P < 1. */
+int64_t svm_request_footprint(int64_t n, int P, const svm_opts *opts);
+/* Drains, stops the workers and frees the server. */
+void svm_server_destroy(svm_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

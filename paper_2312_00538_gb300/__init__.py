@@ -76,6 +76,13 @@ _SIGNATURES = {
     "svm_opts_default": (None, [_vp]),
     "svm_ipm_solve": (_c_int, [_dp, _c_i64, _c_int, _dp, _c_dbl, _c_dbl, _vp, _dp, _dp, _vp]),
     "svm_ipm_solve_batch": (_c_int, [_vp, _c_int, _c_dbl, _vp, _c_int]),
+    "svm_server_create": (_c_int, [_vp, _c_dbl, _c_int, _c_i64, ctypes.POINTER(_vp)]),
+    "svm_server_submit": (_c_int, [_vp, _vp, _lp]),
+    "svm_server_wait": (_c_int, [_vp, _c_i64]),
+    "svm_server_drain": (_c_int, [_vp]),
+    "svm_server_get_stats": (_c_int, [_vp, _vp]),
+    "svm_request_footprint": (_c_i64, [_c_i64, _c_int, _vp]),
+    "svm_server_destroy": (None, [_vp]),
     "anova_last_error": (ctypes.c_char_p, []),
     "anova_version": (ctypes.c_char_p, []),
 }
@@ -444,3 +451,94 @@ def svm_ipm_solve_batch(problems, tol, opts=None, concurrency=8):
         out.append((alphas[i], arr[i].b, arr[i].stats.as_dict(), st))
     del keep
     return out
+
+
+class svm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("reserved_bytes", ctypes.c_int64), ("peak_reserved_bytes", ctypes.c_int64),
+                ("p50_latency_ms", ctypes.c_double), ("p99_latency_ms", ctypes.c_double),
+                ("mean_latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def _fill_problem(pr, X, y, C, ell, windows):
+    """Fill one svm_problem from host arrays; returns the arrays it points into."""
+    X = _f64(X)
+    y = _f64(y)
+    al = np.zeros(X.shape[0])
+    keep = [X, y, al]
+    pr.X = _ptr(X, ctypes.c_double)
+    pr.n = X.shape[0]
+    pr.d = X.shape[1]
+    pr.y = _ptr(y, ctypes.c_double)
+    pr.C = float(C)
+    pr.ell = float(ell or 0.0)
+    if windows is not None:
+        W = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 3)
+        keep.append(W)
+        pr.windows = _ptr(W, ctypes.c_int32)
+        pr.P = W.shape[0]
+    pr.alpha = _ptr(al, ctypes.c_double)
+    return keep
+
+
+def svm_request_footprint(n, P, opts=None):
+    o = opts if opts is not None else svm_opts_default()
+    return int(lib().svm_request_footprint(int(n), int(P), ctypes.byref(o)))
+
+
+class SvmServer:
+    """svm_server_t: queued SVM solves admitted by free slot and device-memory budget.
+
+    submit() returns a ticket at once; wait(ticket) returns (alpha, b, stats dict, status)."""
+
+    def __init__(self, tol, opts=None, slots=8, hbm_budget_bytes=64 << 30):
+        self.opts = opts if opts is not None else svm_opts_default()
+        h = _vp()
+        _check(lib().svm_server_create(ctypes.byref(self.opts), float(tol), int(slots),
+                                       int(hbm_budget_bytes), ctypes.byref(h)))
+        self.handle = h
+        self._pending = {}
+
+    def submit(self, X, y, C, ell=None, windows=None):
+        pr = svm_problem()
+        keep = _fill_problem(pr, X, y, C, ell, windows)
+        t = ctypes.c_int64()
+        _check(lib().svm_server_submit(self.handle, ctypes.byref(pr), ctypes.byref(t)))
+        self._pending[t.value] = (pr, keep)
+        return t.value
+
+    def wait(self, ticket):
+        pr, keep = self._pending[ticket]
+        st = lib().svm_server_wait(self.handle, int(ticket))
+        del self._pending[ticket]
+        if st not in (ANOVA_OK, ANOVA_ERR_NOT_CONVERGED):
+            raise AnovaError(st, "request %d failed" % ticket)
+        return keep[2], pr.b, pr.stats.as_dict(), st
+
+    def drain(self):
+        _check(lib().svm_server_drain(self.handle))
+
+    def stats(self):
+        s = svm_server_stats()
+        _check(lib().svm_server_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def destroy(self):
+        if self.handle:
+            lib().svm_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def svm_server_create(tol, opts=None, slots=8, hbm_budget_bytes=64 << 30):
+    return SvmServer(tol, opts, slots, hbm_budget_bytes)

@@ -24,7 +24,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for m in re.finditer(r"^\s*(?:anova_status|void|const char \*)\s*\*?\s*(\w+)\s*\(", txt, re.M):
+        for m in re.finditer(r"^\s*(?:anova_status|void|int64_t|const char \*)\s*\*?\s*(\w+)\s*\(", txt, re.M):
             names.add(m.group(1))
     return names
 

@@ -48,3 +48,33 @@ def test_invalid_solver_arguments(ab, case):
     with pytest.raises(ab.AnovaError) as ei:
         ab.svm_ipm_solve(X, y, C, tol, opts=o)
     assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", ["slots0", "slots_big", "budget", "tol"])
+def test_invalid_server_arguments(ab, case):
+    slots, budget, tol = 2, 1 << 30, 1e-6
+    if case == "slots0":
+        slots = 0
+    if case == "slots_big":
+        slots = 1000
+    if case == "budget":
+        budget = 0
+    if case == "tol":
+        tol = -1.0
+    with pytest.raises(ab.AnovaError) as ei:
+        ab.SvmServer(tol, slots=slots, hbm_budget_bytes=budget)
+    assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
+
+
+def test_request_footprint(ab):
+    """The admission estimate grows with n, the window count and the rank, and covers at least
+    the FP64 + FP32 low-rank factor and the FP64 plan's grids."""
+    o = ab.svm_opts_default()
+    f = ab.svm_request_footprint
+    assert f(0, 3, o) == 0 and f(100, 0, o) == 0
+    assert f(10_000, 3, o) < f(20_000, 3, o) < f(20_000, 4, o)
+    hi = ab.svm_opts_default()
+    hi.rank = 400
+    assert f(20_000, 3, o) < f(20_000, 3, hi)
+    n, P, r = 50_000, 3, o.rank
+    assert f(n, P, o) >= n * r * 12 + 8 * 4 * P * (2 * o.N_precise) ** 3
