@@ -51,10 +51,17 @@ typedef enum {
     ANOVA_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
 } anova_status;
 
-/* Plan precision flags (anova_nfft_plan `flags`). v and Kv use the same element type. */
+/* Plan flags (anova_nfft_plan `flags`): one precision, optionally one interpolation choice.
+ * v and Kv use the plan's element type. The interpolation choice only matters for FP32 plans with
+ * 3-feature windows and m = 4, which have two kernels computing the same sums: one on the FP32
+ * pipe, one forming the inner sums along the last axis on the tensor cores (tf32 operands split
+ * into high and low parts, FP32 accumulation). By default the plan picks per window group: the
+ * tensor-core kernel when work items hold at least 512 points on average. */
 enum {
-    ANOVA_FP32 = 0, /* float spread / FFT / interpolation with float accumulation */
-    ANOVA_FP64 = 1  /* double everywhere (the "precise" plan) */
+    ANOVA_FP32 = 0,          /* float spread / FFT / interpolation with float accumulation */
+    ANOVA_FP64 = 1,          /* double everywhere (the "precise" plan) */
+    ANOVA_INTERP_TENSOR = 2, /* always the tensor-core interpolation where the plan has it */
+    ANOVA_INTERP_SIMT = 4    /* never the tensor-core interpolation */
 };
 
 /* Low-rank preconditioner kinds (lowrank_precond_build `kind`). */
@@ -74,7 +81,8 @@ enum {
  * m       window cut-off of the NFFT (Sec. 3, O(m^d n)); the Kaiser-Bessel window covers 2m
  *         grid points per dimension on an oversampled grid of n_os = 2N points.
  *         FP32 plans accept 2 <= m <= 6, FP64 plans 3 <= m <= 8.
- * flags   ANOVA_FP32 or ANOVA_FP64.
+ * flags   ANOVA_FP32 or ANOVA_FP64, optionally | ANOVA_INTERP_TENSOR or | ANOVA_INTERP_SIMT
+ *         (not both).
  * cuda_stream  a cudaStream_t (or NULL) on which every later call of this plan is issued.
  * out     receives the plan. The plan copies what it needs; `points` may be freed on return.
  *
@@ -181,6 +189,15 @@ enum {
 };
 anova_status anova_plan_set_timing(anova_plan_t plan, int enable);
 anova_status anova_plan_stage_times(anova_plan_t plan, double *ms, int64_t *launches);
+
+/*
+ * Synchronises the plan's stream and reports kernel-side failures of the calls made so far:
+ * ANOVA_ERR_TIMEOUT if a bounded wait inside a kernel ran out (the affected outputs are not
+ * valid; the flag stays set), ANOVA_ERR_CUDA for the stream's CUDA error; ANOVA_OK otherwise. Kernels never trap or
+ * spin without bound: a tensor-core completion that does not arrive within about a second makes
+ * the kernel skip the dependent work, set the flag and return.
+ */
+anova_status anova_plan_check(anova_plan_t plan);
 
 /* Release a plan and its device memory (NULL is ignored). Synchronises its stream. */
 void anova_plan_destroy(anova_plan_t plan);

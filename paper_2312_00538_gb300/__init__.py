@@ -28,6 +28,8 @@ STATUS_NAMES = {0: "ANOVA_OK", 1: "ANOVA_ERR_INVALID_ARG", 2: "ANOVA_ERR_OUT_OF_
 
 ANOVA_FP32 = 0
 ANOVA_FP64 = 1
+ANOVA_INTERP_TENSOR = 2
+ANOVA_INTERP_SIMT = 4
 PCHOL_GREEDY = 0
 NYSTROM = 1
 
@@ -63,6 +65,7 @@ _SIGNATURES = {
     "anova_plan_info": (_c_int, [_vp, _lp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                  ctypes.POINTER(_c_int), _lp]),
     "anova_plan_destroy": (None, [_vp]),
+    "anova_plan_check": (_c_int, [_vp]),
     "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
     "anova_kernel_coeffs": (_c_int, [_c_dbl, _c_int, _dp]),
@@ -250,6 +253,10 @@ def anova_plan_info(plan):
     _check(lib().anova_plan_info(plan.handle, ctypes.byref(n), ctypes.byref(P), ctypes.byref(nos),
                                  ctypes.byref(fl), ctypes.byref(nb)))
     return dict(n=n.value, P=P.value, n_os=nos.value, flags=fl.value, device_bytes=nb.value)
+
+
+def anova_plan_check(plan):
+    _check(lib().anova_plan_check(plan.handle))
 
 
 def anova_plan_destroy(plan):

@@ -109,6 +109,10 @@ struct anova_plan {
     anova::DevWindow *dwin = nullptr;
     void *D1br = nullptr;         // T[P][3][n_os]: deconvolution diagonal per axis, bit-reversed
     void *tw = nullptr;           // T[n_os]: twiddles (re, im) pairs for k < n_os/2
+    int *dev_status = nullptr;    // [0]: kernel-side error bits (a bounded tensor-core wait ran
+                                  // out); [1 + r]: work counter of RHS r of a persistent launch
+    int sm_count = 0;
+    int interp_flags = 0;         // ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT as created
     int64_t static_bytes = 0;
 
     // workspace, grown on demand

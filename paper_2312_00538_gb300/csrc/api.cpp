@@ -226,9 +226,21 @@ anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, i
     if (n) *n = plan->n;
     if (P) *P = plan->P;
     if (n_os) *n_os = plan->n_os;
-    if (flags) *flags = plan->prec;
+    if (flags) *flags = plan->prec | plan->interp_flags;
     if (device_bytes) *device_bytes = plan->static_bytes + plan->ws_bytes;
     return ANOVA_OK;
+}
+
+anova_status anova_plan_check(anova_plan_t plan) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        DeviceGuard g(plan->device);
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+        int flag = 0;
+        ANOVA_CUDA_TRY(cudaMemcpy(&flag, plan->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) return fail(ANOVA_ERR_TIMEOUT, "a bounded tensor-core wait inside a kernel ran out");
+        return ANOVA_OK;
+    });
 }
 
 void anova_plan_destroy(anova_plan_t plan) {

@@ -9,6 +9,11 @@
 
 namespace anova {
 
+constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core form
+#ifndef ANOVA_INTERP_VARIANT
+// FP32 3-D interpolation with m = 4: 2 = tensor cores where chosen, 0 = always one point per lane
+#define ANOVA_INTERP_VARIANT 2
+#endif
 #ifndef ANOVA_SPREAD_LPP
 #define ANOVA_SPREAD_LPP 32  // lanes per point in the packed FP32 spread (16 or 32)
 #endif
@@ -84,6 +89,37 @@ cudaError_t launch_interp3_x2(const InterpWiArgs &a, int nblocks, int nrhs, cuda
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
     kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm_count, cudaStream_t st) {
+    using C = InterpTcCfg<M, Prec<float>::B>;
+    auto kern = k_interp3_tc<M, Prec<float>::B>;
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (configured != cudaSuccess) return configured;
+    // resident CTAs per SM from the kernel's registers and shared memory, capped by tensor memory
+    // (512 columns per SM): a CTA beyond the cap would wait in its allocation until others exit
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        const int by_regs = regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * 128);
+        const int by_smem = smem_sm / std::max(1, (int)(C::smem + fa.sharedSizeBytes) + smem_res);
+        per_sm = std::max(1, std::min(std::min(by_regs, by_smem), (int)(512 / C::TMEM_COLS)));
+    }
+    // persistent CTAs take work items from the per-RHS counters a.status[1 + r]
+    cudaError_t e = cudaMemsetAsync(a.status + 1, 0, sizeof(int) * kStatusCounters, st);
+    if (e != cudaSuccess) return e;
+    const int nblocks = std::max(1, std::min(nwork, per_sm * std::max(sm_count, 1)));
+    kern<<<dim3(nblocks, nrhs), 128, C::smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -425,8 +461,18 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
             xa.n_os = p->n_os;
             xa.part_w0 = w0;
             xa.wp = wp;
-            cudaError_t e = p->m == 4 ? launch_interp3_x2<4>(xa, wi1 - wi0, nrhs, st)
-                                      : launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
+            xa.status = p->dev_status;
+            cudaError_t e;
+            // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
+            // points; it is used when work items are well filled (large n), else the SIMT form
+            const bool tc_fill = (p->interp_flags & ANOVA_INTERP_TENSOR) ||
+                                 (!(p->interp_flags & ANOVA_INTERP_SIMT) &&
+                                  (double)p->n * (a1 - a0) >= (double)kTcMinPointsPerItem * (wi1 - wi0));
+            if (p->m == 4)
+                e = ANOVA_INTERP_VARIANT == 2 && tc_fill ? launch_interp3_tc<4>(xa, wi1 - wi0, nrhs, p->sm_count, st)
+                                                         : launch_interp3_x2<4>(xa, wi1 - wi0, nrhs, st);
+            else
+                e = launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "interp launch");
             p->launches += 1;
         } else if (sizeof(T) == 8 && s1 > s0) {

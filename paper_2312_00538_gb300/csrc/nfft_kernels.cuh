@@ -12,7 +12,17 @@
 // bit-for-bit reproducible.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels_common.cuh"
+#include "tcgen05.cuh"
+
+#ifndef ANOVA_TC_INTERP_MINB
+#define ANOVA_TC_INTERP_MINB 4  // resident CTAs per SM the tensor-core interpolation is compiled for
+#endif
+#ifndef ANOVA_SPREAD_UNROLL
+#define ANOVA_SPREAD_UNROLL 8  // points per unrolled group of the packed FP32 spread's inner loop
+#endif
 
 namespace anova {
 
@@ -192,6 +202,8 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
     using C = SpreadX2Cfg<M, B, NWARP, LPP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
     constexpr int PPS = 32 / LPP;  // points per warp step
+    constexpr int SPREAD_UNROLL = ANOVA_SPREAD_UNROLL / PPS > 0 ? ANOVA_SPREAD_UNROLL / PPS : 1;
+    static_assert(32 % (PPS * SPREAD_UNROLL) == 0, "unrolled steps stay inside the staged batch");
     static_assert(LPP % W2 == 0 && RPL * LPP == W2 * W2, "2M must divide the lanes per point");
     static_assert(W2 % 4 == 0, "vector staging layout");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -304,9 +316,13 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
                 for (int c = 0; c < W2; c += 4) dst[(C::ZO + c) / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
             }
             __syncwarp();
+            // steps in groups of SPREAD_UNROLL: lanes past the batch staged zero Z weights, so
+            // the padded steps add zeros and the unrolled group needs no remainder loop
             const int nstep = (cnt + PPS - 1) / PPS;
-#pragma unroll 2
-            for (int jj = 0; jj < nstep; ++jj) {
+            for (int j0 = 0; j0 < nstep; j0 += SPREAD_UNROLL)
+#pragma unroll
+            for (int ju = 0; ju < SPREAD_UNROLL; ++ju) {
+                const int jj = j0 + ju;
                 const float *pw = wts + (PPS * jj + half) * PS;
                 float xr[RPL];
                 f32x2 z2[W2 / 2];
@@ -661,6 +677,7 @@ struct InterpWiArgs {
     long long n, total, grid_stride_rhs;
     int nrhs, wi_begin, wi_end, n_os, part_w0;
     WinParams wp;
+    int *status;             // error bits (tensor-core path: a bounded wait ran out)
 };
 
 template <int M, int B, int NWARP>
@@ -762,6 +779,295 @@ __global__ void __launch_bounds__(NWARP * 32) k_interp3_x2(InterpWiArgs a) {
         pi = npi;
         loc = nloc;
     }
+}
+
+// ------------------------------------------------------------------ FP32 3-D interpolation, tensor cores
+// For points p whose cells share the first two cell coordinates (a "column" of up to B cells
+// along the last axis, consecutive in sorted order), the inner sums along the last axis,
+// h_p[a, b] = sum_c z_p[c] g[l0 + a, l1 + b, l2_p + c], are one matrix product: the points' window
+// weights placed at their cell's offset l2_p in a row of 16 (the column's 11 grid values padded)
+// times the column's 64 x 16 block of the bin neighbourhood. A CTA of four warps takes up to 128
+// points of one column at a time (a chunk) and has the tensor cores form all their 64 inner sums
+// (tcgen05.mma kind::tf32, M = 128, N = 64, K = 2 x 8; both operands split into a tf32 high part
+// and an FP32 remainder so that hi*hi + hi*lo + lo*hi carries ~22 significant bits; FP32
+// accumulation in tensor memory). Each thread then reads its point's 64 sums from tensor memory
+// and finishes sum_a x_a sum_b y_b h[a, b] on the FP32 pipe. Chunks are software-pipelined over two
+// operand buffers and two accumulators (the product of one chunk runs while the previous chunk's
+// sums are finished and the next chunk's inputs load). CTAs are persistent and take work items
+// from a counter. Every completion wait is bounded and reports through a.status.
+template <int M, int B>
+struct InterpTcCfg {
+    static constexpr int W2 = 2 * M;
+    static constexpr int TW = B + W2 - 1;
+    static constexpr int TV = TW * TW * TW;
+    static constexpr int TVP = (TV + 3) / 4 * 4;
+    static constexpr int ROWS = 128;                 // points per chunk (MMA M)
+    static constexpr int NCOL = W2 * W2;             // rows (a, b) of the column block (MMA N)
+    static constexpr int KC = 16;                    // column length TW padded to two K = 8 steps
+    static constexpr uint32_t A_BYTES = ROWS * KC * 4, B_BYTES = NCOL * KC * 4;
+    // two buffers of {A hi, A lo} and of {B hi, B lo}, the neighbourhood, barriers, TMEM slot, work
+    static constexpr uint32_t A0 = 0, B0 = 4 * A_BYTES, TILE = B0 + 4 * B_BYTES, MBAR = TILE + TVP * 4,
+                              SLOT = MBAR + 16, WORK = SLOT + 4;
+    static constexpr size_t smem = SLOT + 16;
+    static constexpr uint32_t kMaxPolls = 1u << 22;
+    static constexpr uint32_t TMEM_COLS = 2 * NCOL;  // two accumulators
+    static_assert(TW <= KC, "a column fits in two K = 8 steps");
+};
+
+// per-RHS work counters of the persistent tensor-core kernels live after the status word
+constexpr int kStatusCounters = 16;
+
+template <int M, int B>
+__global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(InterpWiArgs a) {
+    using C = InterpTcCfg<M, B>;
+    constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS, KC = C::KC;
+    static_assert(W2 == 8 && C::NCOL == 64 && B == 4, "layout written for m = 4, B = 4");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw + C::TILE);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + C::MBAR);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem_raw + C::SLOT);
+    int *work_s = reinterpret_cast<int *>(smem_raw + C::WORK);
+
+    const int r = blockIdx.y;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) tc::tmem_alloc(slot, C::TMEM_COLS);
+    if (t == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init_fence();
+    }
+    // operand rows past a chunk's end (and the pad of B) are read by the product: keep them finite
+    for (int i = t; i < (int)(C::TILE / 4); i += 128) reinterpret_cast<float *>(smem_raw)[i] = 0.0f;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t sbase = tc::smem_u32(smem_raw);
+    constexpr uint32_t idesc = tc::idesc_tf32(ROWS, C::NCOL);
+    const float *fr0 = a.frac, *fr1 = a.frac + a.total, *fr2 = a.frac + 2 * a.total;
+    int *counter = a.status + 1 + r;
+    const int nwork = a.wi_end - a.wi_begin;
+    // this thread's B entries: row n = t / 2 (a = n / 8, b = n % 8), K half t % 2 (8 values)
+    const int bn = t >> 1, bkh = t & 1;
+    const int ba = bn >> 3, bb = bn & 7;
+
+    uint32_t parity = 0u;   // bit b: phase parity of barrier b
+    uint32_t pending = 0u;  // bit b: a product committed to barrier b is not yet waited for
+    int buf = 0;
+    bool alive = true;
+
+    struct Chunk {
+        int q0, cnt, l0, l1;
+    };
+    // per-thread inputs of one chunk
+    struct Raw {
+        float f[3];
+        int pi, l2;
+    };
+
+    while (alive) {
+        if (t == 0) *work_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int k = *work_s;
+        if (k >= nwork) break;
+        const int wi_idx = a.wi_begin + k;
+        const int4 wi = a.wis[wi_idx];
+        const int w = wi.x;
+        const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
+        const DevWindow dw = a.dwin[w];
+        const float *grid = a.grid + (size_t)r * a.grid_stride_rhs + dw.grid_off;
+        float *out = a.part + ((size_t)(w - a.part_w0) * a.nrhs + r) * a.n;
+        {
+            const int o0 = bin[0] * B - M + 1, o1 = bin[1] * B - M + 1, o2 = bin[2] * B - M + 1;
+            for (int e = t; e < C::TV; e += 128) {
+                const int z = e % TW, y = (e / TW) % TW, x = e / (TW * TW);
+                tile[e] = grid[((long long)(o0 + x) * a.n_os + (o1 + y)) * a.n_os + (o2 + z)];
+            }
+        }
+        __syncthreads();
+
+        // chunk cursor over the item's segments: up to ROWS consecutive points of one column
+        int cs = wi.y, coff = 0;
+        auto form = [&](Chunk &ch) {
+            ch.cnt = 0;
+            if (cs >= wi.z) return;
+            int4 sg = a.segs[cs];
+            const int cx = cell_coord(sg.x, 0), cy = cell_coord(sg.x, 1);
+            ch.q0 = sg.y + coff;
+            ch.l0 = cx - bin[0] * B;
+            ch.l1 = cy - bin[1] * B;
+            while (true) {
+                const int take = min(sg.z - coff, ROWS - ch.cnt);
+                ch.cnt += take;
+                coff += take;
+                if (coff == sg.z) {
+                    ++cs;
+                    coff = 0;
+                    if (cs >= wi.z) break;
+                    sg = a.segs[cs];
+                    if (cell_coord(sg.x, 0) != cx || cell_coord(sg.x, 1) != cy) break;
+                }
+                if (ch.cnt == ROWS) break;
+            }
+        };
+        auto load_raw = [&](const Chunk &ch, Raw &rw) {
+            if (t < ch.cnt) {
+                const int q = ch.q0 + t;
+                rw.f[0] = fr0[q];
+                rw.f[1] = fr1[q];
+                rw.f[2] = fr2[q];
+                rw.pi = a.perm[q];
+                rw.l2 = a.cellloc[q] % B;
+            }
+        };
+        // window weights (x, y kept for the epilogue) and both operands of one chunk
+        auto stage = [&](int bf, const Chunk &ch, const Raw &rw, float (&wx)[W2], float (&wy)[W2]) {
+            unsigned char *abuf = smem_raw + C::A0 + bf * 2 * C::A_BYTES;
+            unsigned char *bbuf = smem_raw + C::B0 + bf * 2 * C::B_BYTES;
+            if (t < ch.cnt) {
+                float wz[W2];
+                Weights<float, M>::eval(rw.f[0], a.wp, wx);
+                Weights<float, M>::eval(rw.f[1], a.wp, wy);
+                Weights<float, M>::eval(rw.f[2], a.wp, wz);
+                float hi[W2], lo[W2];
+#pragma unroll
+                for (int j = 0; j < W2; ++j) tc::split_tf32(wz[j], hi[j], lo[j]);
+                // the row holds z at positions l2 .. l2 + 7 of 16 (the rest zero)
+                auto put = [&](auto shift_tag) {
+                    constexpr int SH = decltype(shift_tag)::value;
+                    float vh[KC], vl[KC];
+#pragma unroll
+                    for (int c = 0; c < KC; ++c) {
+                        vh[c] = (c >= SH && c < SH + W2) ? hi[c - SH] : 0.0f;
+                        vl[c] = (c >= SH && c < SH + W2) ? lo[c - SH] : 0.0f;
+                    }
+#pragma unroll
+                    for (int c4 = 0; c4 < KC; c4 += 4) {
+                        *reinterpret_cast<float4 *>(abuf + tc::operand_offset16(t, c4)) =
+                            make_float4(vh[c4], vh[c4 + 1], vh[c4 + 2], vh[c4 + 3]);
+                        *reinterpret_cast<float4 *>(abuf + C::A_BYTES + tc::operand_offset16(t, c4)) =
+                            make_float4(vl[c4], vl[c4 + 1], vl[c4 + 2], vl[c4 + 3]);
+                    }
+                };
+                switch (rw.l2) {
+                    case 0: put(std::integral_constant<int, 0>()); break;
+                    case 1: put(std::integral_constant<int, 1>()); break;
+                    case 2: put(std::integral_constant<int, 2>()); break;
+                    default: put(std::integral_constant<int, 3>()); break;
+                }
+            }
+            const float *src = tile + ((ch.l0 + ba) * TW + (ch.l1 + bb)) * TW;
+            float hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = 8 * bkh + j;
+                tc::split_tf32(c < TW ? src[c < TW ? c : 0] : 0.0f, hi[j], lo[j]);
+            }
+#pragma unroll
+            for (int j4 = 0; j4 < 8; j4 += 4) {
+                *reinterpret_cast<float4 *>(bbuf + tc::operand_offset16(bn, 8 * bkh + j4)) =
+                    make_float4(hi[j4], hi[j4 + 1], hi[j4 + 2], hi[j4 + 3]);
+                *reinterpret_cast<float4 *>(bbuf + C::B_BYTES + tc::operand_offset16(bn, 8 * bkh + j4)) =
+                    make_float4(lo[j4], lo[j4 + 1], lo[j4 + 2], lo[j4 + 3]);
+            }
+        };
+        auto issue = [&](int bf) {
+            const uint32_t ab = sbase + C::A0 + bf * 2 * C::A_BYTES, bbase = sbase + C::B0 + bf * 2 * C::B_BYTES;
+            const uint32_t d = tmem + (uint32_t)(bf * C::NCOL);
+            tc::fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t ko = 256u * ks;
+                const uint64_t ahi = tc::smem_desc(ab + ko, 128, 512), alo = tc::smem_desc(ab + C::A_BYTES + ko, 128, 512);
+                const uint64_t bhi = tc::smem_desc(bbase + ko, 128, 512), blo = tc::smem_desc(bbase + C::B_BYTES + ko, 128, 512);
+                tc::mma_tf32(d, ahi, bhi, idesc, ks > 0);
+                tc::mma_tf32(d, ahi, blo, idesc, true);
+                tc::mma_tf32(d, alo, bhi, idesc, true);
+            }
+            tc::mma_commit(&mbar[bf]);
+        };
+        // finish chunk `ch` whose product went to accumulator bf
+        auto finish = [&](int bf, const Chunk &ch, const Raw &rw, const float (&wx)[W2], const float (&wy)[W2]) -> bool {
+            const bool ok = __syncthreads_and(tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, C::kMaxPolls));
+            if (!ok) return false;
+            parity ^= 1u << bf;
+            pending &= ~(1u << bf);
+            tc::fence_after_sync();
+            const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bf * C::NCOL);
+            float f = 0.0f;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float h[32];
+                tc::tmem_ld32(col + (uint32_t)(32 * half), h);
+#pragma unroll
+                for (int aa = 0; aa < 4; ++aa) {
+                    float sb = 0.0f;
+#pragma unroll
+                    for (int b2 = 0; b2 < W2; ++b2) sb = fmaf(wy[b2], h[aa * W2 + b2], sb);
+                    f = fmaf(wx[4 * half + aa], sb, f);
+                }
+            }
+            if (t < ch.cnt) out[rw.pi] = f;
+            tc::fence_before_sync();
+            return true;
+        };
+        // one pipeline step: stage and start chunk `nx` (if any) into buffer bf ^ 1, load the
+        // inputs of the chunk after it, finish chunk `cu` from buffer bf
+        auto step = [&](Chunk &cu, Raw &rcu, float (&wxc)[W2], float (&wyc)[W2], Chunk &nx, Raw &rnx,
+                        float (&wxn)[W2], float (&wyn)[W2], Chunk &nn, Raw &rnn) -> int {
+            const bool have_next = nx.cnt > 0;
+            if (have_next) stage(buf ^ 1, nx, rnx, wxn, wyn);
+            form(nn);
+            load_raw(nn, rnn);
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (have_next) {
+                if (t == 0) issue(buf ^ 1);
+                pending |= 1u << (buf ^ 1);
+            }
+            if (!finish(buf, cu, rcu, wxc, wyc)) return -1;
+            buf ^= 1;
+            return have_next ? 1 : 0;
+        };
+
+        Chunk c0, c1, c2;
+        Raw r0, r1, r2;
+        float wx0[W2], wy0[W2], wx1[W2], wy1[W2];
+        form(c0);
+        load_raw(c0, r0);
+        stage(buf, c0, r0, wx0, wy0);
+        form(c1);
+        load_raw(c1, r1);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (t == 0) issue(buf);
+        pending |= 1u << buf;
+        // ping-pong between the two register sets; c2/r2 receive the chunk after next
+        int st;
+        while (true) {
+            st = step(c0, r0, wx0, wy0, c1, r1, wx1, wy1, c2, r2);
+            if (st <= 0) break;
+            c0 = c2;
+            r0 = r2;
+            st = step(c1, r1, wx1, wy1, c0, r0, wx0, wy0, c2, r2);
+            if (st <= 0) break;
+            c1 = c2;
+            r1 = r2;
+        }
+        if (st < 0) {
+            if (t == 0) atomicOr(a.status, 1);
+            alive = false;
+        }
+    }
+    if (!alive) {
+        // a completion that never arrived: one more bounded wait on each barrier's pending
+        // phase before the accumulator columns are released
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) tc::mbar_wait_bounded(&mbar[b], (parity >> b) & 1u, C::kMaxPolls);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
 // ------------------------------------------------------------------ interpolation, any dims

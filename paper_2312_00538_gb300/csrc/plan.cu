@@ -219,7 +219,7 @@ void destroy_plan(anova_plan *p) {
     cudaStreamSynchronize(p->stream);
     release_workspace(p);
     void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->bins, p->mbins, p->ftiles, p->dwin,
-                    p->D1br, p->tw, p->dv, p->dkv};
+                    p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -237,7 +237,8 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     if (P < 1 || P > kMaxWindows) return fail(ANOVA_ERR_INVALID_ARG, "P must be in [1, 64]");
     if ((int64_t)n * P > ((int64_t)1 << 31) - 1) return fail(ANOVA_ERR_INVALID_ARG, "n * P exceeds 2^31 - 1");
     const int prec = flags & 1;
-    if (flags & ~1) return fail(ANOVA_ERR_INVALID_ARG, "unknown flag bits");
+    if (flags & ~7) return fail(ANOVA_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & 6) == 6) return fail(ANOVA_ERR_INVALID_ARG, "ANOVA_INTERP_TENSOR and ANOVA_INTERP_SIMT both set");
     if (N != 16 && N != 32 && N != 64 && N != 128)
         return fail(ANOVA_ERR_INVALID_ARG, "N must be an even power of two in {16, 32, 64, 128}");
     if (prec == ANOVA_FP32 ? (m < 2 || m > 6) : (m < 3 || m > 6))
@@ -287,6 +288,7 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     p->m = m;
     p->n_os = 2 * N;
     p->prec = prec;
+    p->interp_flags = flags & 6;
     p->B = prec == ANOVA_FP64 ? 2 : 4;
     p->NB = p->n_os / p->B;
     p->tile_w = p->B + 2 * m - 1;
@@ -635,6 +637,9 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     }
     if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * 32)) != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * 32, st));
+    ANOVA_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
     std::vector<float> f32;
     if (prec == ANOVA_FP64) {
         if ((s = upload(&p->D1br, d1br.data(), sizeof(double) * d1br.size())) != ANOVA_OK) return s;

@@ -72,7 +72,9 @@ def test_invalid_arguments_are_rejected_before_any_device_work(ab):
         (dict(points=X + 0.3, windows=W, sigma=1.0), ab.ANOVA_ERR_OUT_OF_RANGE),
         (dict(points=np.where(np.eye(4, 3) > 0, np.nan, 0.0), windows=W, sigma=1.0),
          ab.ANOVA_ERR_NONFINITE),
-        (dict(points=X, windows=W, sigma=1.0, flags=4), ab.ANOVA_ERR_INVALID_ARG),
+        (dict(points=X, windows=W, sigma=1.0, flags=8), ab.ANOVA_ERR_INVALID_ARG),
+        (dict(points=X, windows=W, sigma=1.0, flags=ab.ANOVA_INTERP_TENSOR | ab.ANOVA_INTERP_SIMT),
+         ab.ANOVA_ERR_INVALID_ARG),
     ]
     for kw, status in cases:
         with pytest.raises(ab.AnovaError) as ei:
