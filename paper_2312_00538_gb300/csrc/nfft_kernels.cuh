@@ -806,8 +806,9 @@ struct InterpTcCfg {
     static constexpr int KC = 16;                    // column length TW padded to two K = 8 steps
     static constexpr uint32_t A_BYTES = ROWS * KC * 4, B_BYTES = NCOL * KC * 4;
     // two buffers of {A hi, A lo} and of {B hi, B lo}, the neighbourhood, barriers, TMEM slot, work
-    static constexpr uint32_t A0 = 0, B0 = 4 * A_BYTES, TILE = B0 + 4 * B_BYTES, MBAR = TILE + TVP * 4,
-                              SLOT = MBAR + 16, WORK = SLOT + 4;
+    static constexpr int SEG_CACHE = 128;            // segments of a work item kept in shared memory
+    static constexpr uint32_t A0 = 0, B0 = 4 * A_BYTES, TILE = B0 + 4 * B_BYTES, SEGS = TILE + TVP * 4,
+                              MBAR = SEGS + SEG_CACHE * 16, SLOT = MBAR + 16, WORK = SLOT + 4;
     static constexpr size_t smem = SLOT + 16;
     static constexpr uint32_t kMaxPolls = 1u << 22;
     static constexpr uint32_t TMEM_COLS = 2 * NCOL;  // two accumulators
@@ -827,6 +828,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + C::MBAR);
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem_raw + C::SLOT);
     int *work_s = reinterpret_cast<int *>(smem_raw + C::WORK);
+    int4 *segs_s = reinterpret_cast<int4 *>(smem_raw + C::SEGS);
 
     const int r = blockIdx.y;
     const int t = threadIdx.x, warp = t >> 5;
@@ -855,6 +857,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     uint32_t pending = 0u;  // bit b: a product committed to barrier b is not yet waited for
     int buf = 0;
     bool alive = true;
+    bool failed = false;    // this thread's bounded wait ran out
 
     struct Chunk {
         int q0, cnt, l0, l1;
@@ -867,7 +870,11 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
 
     while (alive) {
         if (t == 0) *work_s = atomicAdd(counter, 1);
-        __syncthreads();
+        if (__syncthreads_or(failed)) {
+            alive = false;
+            if (t == 0) atomicOr(a.status, 1);
+            break;
+        }
         const int k = *work_s;
         if (k >= nwork) break;
         const int wi_idx = a.wi_begin + k;
@@ -884,14 +891,19 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                 tile[e] = grid[((long long)(o0 + x) * a.n_os + (o1 + y)) * a.n_os + (o2 + z)];
             }
         }
+        // the item's segments (the chunk walk reads them serially)
+        const bool seg_cached = wi.z - wi.y <= C::SEG_CACHE;
+        if (seg_cached)
+            for (int i = t; i < wi.z - wi.y; i += 128) segs_s[i] = a.segs[wi.y + i];
         __syncthreads();
+        auto seg_at = [&](int i) -> int4 { return seg_cached ? segs_s[i - wi.y] : a.segs[i]; };
 
         // chunk cursor over the item's segments: up to ROWS consecutive points of one column
         int cs = wi.y, coff = 0;
         auto form = [&](Chunk &ch) {
             ch.cnt = 0;
             if (cs >= wi.z) return;
-            int4 sg = a.segs[cs];
+            int4 sg = seg_at(cs);
             const int cx = cell_coord(sg.x, 0), cy = cell_coord(sg.x, 1);
             ch.q0 = sg.y + coff;
             ch.l0 = cx - bin[0] * B;
@@ -904,7 +916,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                     ++cs;
                     coff = 0;
                     if (cs >= wi.z) break;
-                    sg = a.segs[cs];
+                    sg = seg_at(cs);
                     if (cell_coord(sg.x, 0) != cx || cell_coord(sg.x, 1) != cy) break;
                 }
                 if (ch.cnt == ROWS) break;
@@ -920,14 +932,12 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                 rw.l2 = a.cellloc[q] % B;
             }
         };
-        // window weights (x, y kept for the epilogue) and both operands of one chunk
-        auto stage = [&](int bf, const Chunk &ch, const Raw &rw, float (&wx)[W2], float (&wy)[W2]) {
+        // both operands of one chunk: the points' last-axis weights (A) and the column block (B)
+        auto stage = [&](int bf, const Chunk &ch, const Raw &rw) {
             unsigned char *abuf = smem_raw + C::A0 + bf * 2 * C::A_BYTES;
             unsigned char *bbuf = smem_raw + C::B0 + bf * 2 * C::B_BYTES;
             if (t < ch.cnt) {
                 float wz[W2];
-                Weights<float, M>::eval(rw.f[0], a.wp, wx);
-                Weights<float, M>::eval(rw.f[1], a.wp, wy);
                 Weights<float, M>::eval(rw.f[2], a.wp, wz);
                 float hi[W2], lo[W2];
 #pragma unroll
@@ -987,55 +997,60 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
             tc::mma_commit(&mbar[bf]);
         };
         // finish chunk `ch` whose product went to accumulator bf
-        auto finish = [&](int bf, const Chunk &ch, const Raw &rw, const float (&wx)[W2], const float (&wy)[W2]) -> bool {
-            const bool ok = __syncthreads_and(tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, C::kMaxPolls));
-            if (!ok) return false;
+        // (the first two axes' weights are evaluated here, while the product runs). A thread whose
+        // bounded wait runs out marks itself failed and skips the dependent work; the block agrees
+        // on failures at the next barrier.
+        auto finish = [&](int bf, const Chunk &ch, const Raw &rw) {
+            float wx[W2], wy[W2];
+            Weights<float, M>::eval(rw.f[0], a.wp, wx);
+            Weights<float, M>::eval(rw.f[1], a.wp, wy);
+            if (!tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, C::kMaxPolls)) {
+                failed = true;
+                return;
+            }
             parity ^= 1u << bf;
             pending &= ~(1u << bf);
             tc::fence_after_sync();
             const uint32_t col = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bf * C::NCOL);
             float f = 0.0f;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                float h[32];
-                tc::tmem_ld32(col + (uint32_t)(32 * half), h);
+            for (int q4 = 0; q4 < 4; ++q4) {
+                float h[16];
+                tc::tmem_ld16(col + (uint32_t)(16 * q4), h);
 #pragma unroll
-                for (int aa = 0; aa < 4; ++aa) {
+                for (int aa = 0; aa < 2; ++aa) {
                     float sb = 0.0f;
 #pragma unroll
                     for (int b2 = 0; b2 < W2; ++b2) sb = fmaf(wy[b2], h[aa * W2 + b2], sb);
-                    f = fmaf(wx[4 * half + aa], sb, f);
+                    f = fmaf(wx[2 * q4 + aa], sb, f);
                 }
             }
             if (t < ch.cnt) out[rw.pi] = f;
             tc::fence_before_sync();
-            return true;
         };
         // one pipeline step: stage and start chunk `nx` (if any) into buffer bf ^ 1, load the
         // inputs of the chunk after it, finish chunk `cu` from buffer bf
-        auto step = [&](Chunk &cu, Raw &rcu, float (&wxc)[W2], float (&wyc)[W2], Chunk &nx, Raw &rnx,
-                        float (&wxn)[W2], float (&wyn)[W2], Chunk &nn, Raw &rnn) -> int {
+        auto step = [&](Chunk &cu, Raw &rcu, Chunk &nx, Raw &rnx, Chunk &nn, Raw &rnn) -> int {
             const bool have_next = nx.cnt > 0;
-            if (have_next) stage(buf ^ 1, nx, rnx, wxn, wyn);
+            if (have_next) stage(buf ^ 1, nx, rnx);
             form(nn);
             load_raw(nn, rnn);
             tc::fence_proxy_async();
-            __syncthreads();
+            if (__syncthreads_or(failed)) return -1;
             if (have_next) {
                 if (t == 0) issue(buf ^ 1);
                 pending |= 1u << (buf ^ 1);
             }
-            if (!finish(buf, cu, rcu, wxc, wyc)) return -1;
+            finish(buf, cu, rcu);
             buf ^= 1;
             return have_next ? 1 : 0;
         };
 
         Chunk c0, c1, c2;
         Raw r0, r1, r2;
-        float wx0[W2], wy0[W2], wx1[W2], wy1[W2];
         form(c0);
         load_raw(c0, r0);
-        stage(buf, c0, r0, wx0, wy0);
+        stage(buf, c0, r0);
         form(c1);
         load_raw(c1, r1);
         tc::fence_proxy_async();
@@ -1045,11 +1060,11 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
         // ping-pong between the two register sets; c2/r2 receive the chunk after next
         int st;
         while (true) {
-            st = step(c0, r0, wx0, wy0, c1, r1, wx1, wy1, c2, r2);
+            st = step(c0, r0, c1, r1, c2, r2);
             if (st <= 0) break;
             c0 = c2;
             r0 = r2;
-            st = step(c1, r1, wx1, wy1, c0, r0, wx0, wy0, c2, r2);
+            st = step(c1, r1, c0, r0, c2, r2);
             if (st <= 0) break;
             c1 = c2;
             r1 = r2;
