@@ -68,6 +68,26 @@ cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t 
     return cudaGetLastError();
 }
 
+// CTAs of `kern` (threads per CTA, dynamic shared memory) that fit on one SM at once, from its
+// registers and shared memory, at most `cap`
+template <typename K>
+cudaError_t resident_ctas(K kern, int threads, size_t smem, int cap, int *out) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0, thr_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int by_regs = regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * threads);
+    const int by_smem = smem_sm / std::max(1, (int)(smem + fa.sharedSizeBytes) + smem_res);
+    const int by_thr = thr_sm / std::max(1, threads);
+    *out = std::max(1, std::min(std::min(std::min(by_regs, by_smem), by_thr), cap));
+    return cudaSuccess;
+}
+
 template <int M, int LPP>
 cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
     constexpr int B = Prec<float>::B, NW = Prec<float>::SPREAD_WARPS;
@@ -99,21 +119,12 @@ cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    // resident CTAs per SM from the kernel's registers and shared memory, capped by tensor memory
-    // (512 columns per SM): a CTA beyond the cap would wait in its allocation until others exit
+    // resident CTAs per SM, capped by tensor memory (512 columns per SM): a CTA beyond the cap
+    // would wait in its allocation until others exit
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        cudaError_t e = resident_ctas(kern, 128, C::smem, (int)(512 / C::TMEM_COLS), &per_sm);
         if (e != cudaSuccess) return e;
-        int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        const int by_regs = regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * 128);
-        const int by_smem = smem_sm / std::max(1, (int)(C::smem + fa.sharedSizeBytes) + smem_res);
-        per_sm = std::max(1, std::min(std::min(by_regs, by_smem), (int)(512 / C::TMEM_COLS)));
     }
     // persistent CTAs take work items from the per-RHS counters a.status[1 + r]
     cudaError_t e = cudaMemsetAsync(a.status + 1, 0, sizeof(int) * kStatusCounters, st);
@@ -462,6 +473,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
             xa.part_w0 = w0;
             xa.wp = wp;
             xa.status = p->dev_status;
+            xa.order = p->wi_order;
             cudaError_t e;
             // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
             // points; it is used when work items are well filled (large n), else the SIMT form

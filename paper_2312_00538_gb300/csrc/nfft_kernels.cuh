@@ -678,6 +678,7 @@ struct InterpWiArgs {
     int nrhs, wi_begin, wi_end, n_os, part_w0;
     WinParams wp;
     int *status;             // error bits (tensor-core path: a bounded wait ran out)
+    const int *order;        // persistent kernels: work items of each window, largest first
 };
 
 template <int M, int B, int NWARP>
@@ -877,7 +878,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
         }
         const int k = *work_s;
         if (k >= nwork) break;
-        const int wi_idx = a.wi_begin + k;
+        const int wi_idx = a.order[a.wi_begin + k];
         const int4 wi = a.wis[wi_idx];
         const int w = wi.x;
         const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};

@@ -218,7 +218,7 @@ void destroy_plan(anova_plan *p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->bins, p->mbins, p->ftiles, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->bins, p->mbins, p->ftiles, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -621,6 +621,24 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     anova_status s;
     if ((s = upload((void **)&p->segs, segs.data(), sizeof(int4) * segs.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->wis, wis.data(), sizeof(int4) * wis.size())) != ANOVA_OK) return s;
+    {
+        // each window's work items by decreasing point count (ties by index): persistent kernels
+        // that take items in this order finish on the smallest ones
+        std::vector<int> order(wis.size());
+        for (int w = 0; w < P; ++w) {
+            const int b0 = p->win[w].wi_begin, b1 = p->win[w].wi_end;
+            std::vector<std::pair<int, int>> sz;
+            sz.reserve(b1 - b0);
+            for (int x = b0; x < b1; ++x) {
+                int cnt = 0;
+                for (int sgi = wis[x].y; sgi < wis[x].z; ++sgi) cnt += segs[sgi].z;
+                sz.emplace_back(-cnt, x);
+            }
+            std::sort(sz.begin(), sz.end());
+            for (int i = 0; i < b1 - b0; ++i) order[b0 + i] = sz[i].second;
+        }
+        if ((s = upload((void **)&p->wi_order, order.data(), sizeof(int) * order.size())) != ANOVA_OK) return s;
+    }
     if ((s = upload((void **)&p->bins, bins.data(), sizeof(int2) * bins.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->mbins, mbins.data(), sizeof(int4) * mbins.size())) != ANOVA_OK) return s;
     {
