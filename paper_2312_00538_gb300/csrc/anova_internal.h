@@ -121,7 +121,6 @@ struct anova_plan {
     void *grids = nullptr;        // T[4][ws_rhs][grid_total]
     void *tiles = nullptr;        // T[nwi][ws_rhs][tile_vol]
     void *part = nullptr;         // T[P][ws_rhs][n]
-    void *vsorted = nullptr;      // float[ws_rhs][P n]: v in sorted order (FP32 packed spread)
     int64_t ws_bytes = 0;
     // host-call staging
     void *dv = nullptr, *dkv = nullptr;

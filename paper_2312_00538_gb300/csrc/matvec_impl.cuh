@@ -230,8 +230,8 @@ template <typename T>
 cudaError_t dispatch_spread(int dw, int m, const SpreadArgs &a, int nb, int nrhs, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         // the packed kernel reads v in sorted order; callers without that copy use the generic one
-        if (a.vsorted && dw == 3 && m == 4) return launch_spread3_x2<4, ANOVA_SPREAD_LPP>(a, nb, nrhs, st);
-        if (a.vsorted && dw == 3 && m == 2) return launch_spread3_x2<2, 16>(a, nb, nrhs, st);
+        if (a.packed && dw == 3 && m == 4) return launch_spread3_x2<4, ANOVA_SPREAD_LPP>(a, nb, nrhs, st);
+        if (a.packed && dw == 3 && m == 2) return launch_spread3_x2<2, 16>(a, nb, nrhs, st);
     }
     switch (dw) {
         case 1: return dispatch_spread_m<T, 1>(m, a, nb, nrhs, st);
@@ -375,18 +375,9 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         const int s0 = p->win[a0].seg_begin, s1 = p->win[a1 - 1].seg_end;
         const bool packed = packed_path((int)sizeof(T), gr.dw, p->m);
         cudaEvent_t e0 = stage_event(p);
-        if (packed) {
-            // v in sorted order for the packed spread
-            const long long q0 = (long long)a0 * p->n, q1 = (long long)a1 * p->n;
-            const int nb = (int)std::min<long long>(((q1 - q0) * nrhs + 255) / 256, 152LL * 16);
-            k_gather_v<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float *>(v), p->perm, p->n, p->n * p->P, q0, q1,
-                                           nrhs, reinterpret_cast<float *>(p->vsorted));
-            ANOVA_CUDA_TRY(cudaGetLastError());
-            p->launches += 1;
-        }
         // 1. spread into partial tiles
         SpreadArgs sa;
-        sa.vsorted = packed ? p->vsorted : nullptr;
+        sa.packed = packed ? 1 : 0;
         sa.wis = p->wis;
         sa.segs = p->segs;
         sa.frac = p->frac;

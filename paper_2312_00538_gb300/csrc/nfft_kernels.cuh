@@ -27,7 +27,7 @@
 namespace anova {
 
 struct SpreadArgs {
-    const void *vsorted;    // FP32 packed path: v gathered into sorted order, [nrhs][total]
+    int packed;             // FP32 3-D windows, m = 2 or 4: the packed kernel may be used
     const int4 *wis;        // {window, seg_begin, seg_end, bin packed}
     const int4 *segs;       // {cell packed, sorted start, count, window}
     const void *frac;       // T[3][total]
@@ -194,7 +194,9 @@ struct SpreadX2Cfg {
     static constexpr int TV = TW * TW * TW;
     static constexpr int TVP = (TV + 3) / 4 * 4;
     static constexpr int XO = 0, YO = W2, ZO = 2 * W2, PS = 3 * W2;      // staged floats per point
-    static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS);
+    static constexpr int SEG_CACHE = 128;                               // segments kept in shared memory
+    // warp tiles, staged weights, the item's segments
+    static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS) + 16 * SEG_CACHE;
 };
 
 template <int M, int B, int NWARP, int LPP>
@@ -219,12 +221,19 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
     const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
 
     for (int i = threadIdx.x; i < NWARP * C::TVP; i += NWARP * 32) tiles_s[i] = 0.0f;
+    // the item's segments in shared memory (each warp searches them for its first point and
+    // walks them in order)
+    int4 *segs_s = reinterpret_cast<int4 *>(wts_s + NWARP * 32 * PS);
+    const bool seg_cached = wi.z - wi.y <= C::SEG_CACHE;
+    if (seg_cached)
+        for (int i = threadIdx.x; i < wi.z - wi.y; i += NWARP * 32) segs_s[i] = a.segs[wi.y + i];
     __syncthreads();
+    auto seg_at = [&](int i) -> int4 { return seg_cached ? segs_s[i - wi.y] : a.segs[i]; };
 
     // each warp takes an equal share of the item's points (a cell may be split between two
     // warps; each adds its part into its own tile)
-    const int4 s_first = a.segs[wi.y];
-    const int4 s_last = a.segs[wi.z - 1];
+    const int4 s_first = seg_at(wi.y);
+    const int4 s_last = seg_at(wi.z - 1);
     const int p0 = s_first.y, p1 = s_last.y + s_last.z;
     const int len = p1 - p0;
     const int pw0 = p0 + (int)(((long long)len * warp) / NWARP);
@@ -232,7 +241,10 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
 
     const float *fr0 = reinterpret_cast<const float *>(a.frac);
     const float *fr1 = fr0 + a.total, *fr2 = fr0 + 2 * a.total;
-    const float *vs = reinterpret_cast<const float *>(a.vsorted) + (size_t)r * a.total;
+    // v is read through the permutation: the permutation streams in sorted order and v (4 bytes
+    // per point) stays in L2, so no sorted copy of v is written first
+    const float *vr = reinterpret_cast<const float *>(a.v) + (size_t)r * a.n;
+    auto vsorted_at = [&](int q) { return vr[a.perm[q]]; };
     float *tile = tiles_s + warp * C::TVP;
     float *wts = wts_s + warp * 32 * PS;
     const int g = lh / W2;           // this lane's rows: a = g + S k, b = lh % W2
@@ -244,12 +256,12 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
             int lo = wi.y, hi = wi.z - 1;  // last segment starting at or before pw0
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (a.segs[mid].y <= pw0) lo = mid; else hi = mid - 1;
+                if (seg_at(mid).y <= pw0) lo = mid; else hi = mid - 1;
             }
             s = lo;
         }
-        int4 sg = a.segs[s];
-        int4 sg_next = (s + 1 < wi.z) ? a.segs[s + 1] : sg;
+        int4 sg = seg_at(s);
+        int4 sg_next = (s + 1 < wi.z) ? seg_at(s + 1) : sg;
         int q = pw0;
         int send = min(sg.y + sg.z, pw1);
         int cnt = min(32, send - q);
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
             fx = fr0[q + lane];
             fy = fr1[q + lane];
             fz = fr2[q + lane];
-            vv = vs[q + lane];
+            vv = vsorted_at(q + lane);
         }
         f32x2 acc[RPL][W2 / 2];
 #pragma unroll
@@ -288,10 +300,10 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
                 nfx = fr0[qn + lane];
                 nfy = fr1[qn + lane];
                 nfz = fr2[qn + lane];
-                nvv = vs[qn + lane];
+                nvv = vsorted_at(qn + lane);
             }
             int4 sg_next2 = sg_next;
-            if (newpiece && !done && sn + 1 < wi.z) sg_next2 = a.segs[sn + 1];
+            if (newpiece && !done && sn + 1 < wi.z) sg_next2 = seg_at(sn + 1);
             // stage the current batch's weights (zeros for lanes past the batch)
             {
                 float wx[W2], wy[W2], wz[W2];
@@ -412,18 +424,6 @@ __global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
 #pragma unroll
         for (int w = 0; w < NWARP; ++w) s2 += tiles_s[w * C::TVP + i];
         out[i] = s2;
-    }
-}
-
-// v in sorted order (one copy per window), so that the spread reads it coalesced
-template <typename T>
-__global__ void k_gather_v(const T *__restrict__ v, const int *__restrict__ perm, long long n,
-                           long long total, long long q0, long long q1, int nrhs, T *__restrict__ vs) {
-    const long long cnt = q1 - q0;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt * nrhs;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / cnt, q = q0 + (t - r * cnt);
-        vs[r * total + q] = v[r * n + perm[q]];
     }
 }
 

@@ -50,7 +50,7 @@ anova_status spread_noalloc(anova_plan *p, int w, const void *v, void *grid) {
     cudaStream_t s = p->stream;
 
     SpreadArgs sa;
-    sa.vsorted = nullptr;  // generic spread: no sorted copy of v (that would need workspace)
+    sa.packed = 0;  // the generic spread kernel
     sa.wis = p->wis;
     sa.segs = p->segs;
     sa.frac = p->frac;

@@ -181,8 +181,7 @@ void release_workspace(anova_plan *p) {
     if (p->grids) cudaFree(p->grids);
     if (p->tiles) cudaFree(p->tiles);
     if (p->part) cudaFree(p->part);
-    if (p->vsorted) cudaFree(p->vsorted);
-    p->grids = p->tiles = p->part = p->vsorted = nullptr;
+    p->grids = p->tiles = p->part = nullptr;
     p->ws_rhs = 0;
     p->ws_bytes = 0;
 }
@@ -199,18 +198,16 @@ anova_status ensure_workspace(anova_plan *p, int nrhs) {
     const size_t gbytes = es * 4 * (size_t)nrhs * p->grid_total;
     const size_t tbytes = es * std::max<size_t>(1, (size_t)p->nwi * nrhs * tv);
     const size_t pbytes = es * (size_t)p->P * nrhs * p->n;
-    const size_t vbytes = p->prec == ANOVA_FP32 ? sizeof(float) * (size_t)p->P * nrhs * p->n : 16;
     if ((e = cudaMalloc(&p->grids, gbytes)) != cudaSuccess ||
         (e = cudaMalloc(&p->tiles, tbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&p->part, pbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&p->vsorted, vbytes)) != cudaSuccess) {
+        (e = cudaMalloc(&p->part, pbytes)) != cudaSuccess) {
         release_workspace(p);
         return fail(ANOVA_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
     }
     e = cudaMemsetAsync(p->grids, 0, gbytes, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     p->ws_rhs = nrhs;
-    p->ws_bytes = (int64_t)(gbytes + tbytes + pbytes + vbytes);
+    p->ws_bytes = (int64_t)(gbytes + tbytes + pbytes);
     return ANOVA_OK;
 }
 

@@ -48,11 +48,10 @@ struct svm_server {
 
 extern "C" {
 
-static int64_t plan_bytes(int64_t n, int P, int N, int m, int B, int es, bool fp32) {
+static int64_t plan_bytes(int64_t n, int P, int N, int m, int B, int es) {
     // mirrors the plan's own allocations: sorted keys/perm/fractions/window coordinates,
     // the grids of the fused FFT, the per-work-item tiles (at most one per occupied bin; points
-    // lie in a box of half-width kBoxHalf, i.e. 0.4 of the torus per axis), partial results and
-    // the pre-gathered coefficients of the FP32 path
+    // lie in a box of half-width kBoxHalf, i.e. 0.4 of the torus per axis), partial results
     const int64_t total = n * P;
     const int64_t g = 2 * (int64_t)N;
     const int64_t tw = B + 2 * m - 1;
@@ -62,7 +61,6 @@ static int64_t plan_bytes(int64_t n, int P, int N, int m, int B, int es, bool fp
     b += (int64_t)es * 4 * P * g * g * g;
     b += (int64_t)es * bins * tw * tw * tw;
     b += (int64_t)es * total;
-    if (fp32) b += 4 * total;
     return b;
 }
 
@@ -72,7 +70,7 @@ int64_t svm_request_footprint(int64_t n, int P, const svm_opts *opts) {
     if (opts) o = *opts;
     if (n < 1 || P < 1) return 0;
     const int64_t r = std::min<int64_t>(std::max(o.rank, 1), n);
-    int64_t b = plan_bytes(n, P, o.N, o.m, 4, 4, true) + plan_bytes(n, P, o.N_precise, o.m_precise, 2, 8, false);
+    int64_t b = plan_bytes(n, P, o.N, o.m, 4, 4) + plan_bytes(n, P, o.N_precise, o.m_precise, 2, 8);
     b += n * r * (8 + 4) + r * r * 8 * 2;  // low-rank factor (FP64 + FP32 panel) and Woodbury core
     b += n * 8 * 48;                      // iterates, Krylov vectors and scratch of the solver
     b += n * 8 * 3;                       // the points on the device
