@@ -111,8 +111,13 @@ struct anova_plan {
     void *D1br = nullptr;         // T[P][3][n_os]: deconvolution diagonal per axis, bit-reversed
     void *tw = nullptr;           // T[n_os]: twiddles (re, im) pairs for k < n_os/2
     int *dev_status = nullptr;    // [0]: kernel-side error bits (a bounded tensor-core wait ran
-                                  // out); [1 + r]: work counter of RHS r of a persistent launch
+                                  // out); [1 + 16 k + r]: work counter of RHS r of a persistent
+                                  // launch on window stream k (64 ints)
     int sm_count = 0;
+    // windows of one matvec run concurrently on these streams (forked from and joined back to
+    // `stream`); window w uses aux[w % kAuxStreams] and work-counter block w % kAuxStreams
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_evt = nullptr, join_evt[3] = {nullptr, nullptr, nullptr};
     int interp_flags = 0;         // ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT as created
     int64_t static_bytes = 0;
 

@@ -9,7 +9,11 @@
 
 namespace anova {
 
-constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core form
+#ifndef ANOVA_SPREAD_WARPS
+#define ANOVA_SPREAD_WARPS 8  // warps per CTA of the packed FP32 spread
+#endif
+constexpr int kTcMinPointsPerItem = 512;
+constexpr int kAuxStreams = 3;  // concurrent window chains of one matvec  // mean points per work item for the tensor-core form
 #ifndef ANOVA_INTERP_VARIANT
 // FP32 3-D interpolation with m = 4: 2 = tensor cores where chosen, 0 = always one point per lane
 #define ANOVA_INTERP_VARIANT 2
@@ -23,7 +27,7 @@ struct Prec;
 template <>
 struct Prec<float> {
     static constexpr int B = 4;
-    static constexpr int SPREAD_WARPS = 8;
+    static constexpr int SPREAD_WARPS = ANOVA_SPREAD_WARPS;
     static constexpr int INTERP_WARPS = 8;
 };
 template <>
@@ -126,8 +130,8 @@ cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm
         cudaError_t e = resident_ctas(kern, 128, C::smem, (int)(512 / C::TMEM_COLS), &per_sm);
         if (e != cudaSuccess) return e;
     }
-    // persistent CTAs take work items from the per-RHS counters a.status[1 + r]
-    cudaError_t e = cudaMemsetAsync(a.status + 1, 0, sizeof(int) * kStatusCounters, st);
+    // persistent CTAs take work items from the per-RHS counters a.counters[r]
+    cudaError_t e = cudaMemsetAsync(a.counters, 0, sizeof(int) * kStatusCounters, st);
     if (e != cudaSuccess) return e;
     const int nblocks = std::max(1, std::min(nwork, per_sm * std::max(sm_count, 1)));
     kern<<<dim3(nblocks, nrhs), 128, C::smem, st>>>(a);
@@ -318,8 +322,7 @@ int tile_volume(const anova_plan *p, int dw) {
 // gather of bin tiles onto every grid point of the windows' boxes.
 template <typename T>
 anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, long long grid_stride,
-                           int nrhs, int zero_offset) {
-    cudaStream_t st = p->stream;
+                           int nrhs, int zero_offset, cudaStream_t st) {
     BinReduceArgs ba;
     ba.tiles = p->tiles;
     ba.mbins = p->mbins;
@@ -365,8 +368,7 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
 // per-window results in original point order; grids g[0..3] are the workspace buffers.
 template <typename T>
 anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1, T *part,
-                            T *const g[4], long long grid_stride) {
-    cudaStream_t st = p->stream;
+                            T *const g[4], long long grid_stride, cudaStream_t st, int *counters) {
     const WinParams wp = make_winparams<T>(p);
     for (const Group &gr : p->groups) {
         const int a0 = std::max(gr.w_begin, w0), a1 = std::min(gr.w_end, w1);
@@ -399,7 +401,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         stage_record(p, STAGE_SPREAD, e0, e1);
         // 2. reduce partial tiles onto the grid boxes
         {
-            anova_status rs = launch_reduce<T>(p, gr.dw, a0, a1, g[0], grid_stride, nrhs, 0);
+            anova_status rs = launch_reduce<T>(p, gr.dw, a0, a1, g[0], grid_stride, nrhs, 0, st);
             if (rs != ANOVA_OK) return rs;
         }
         cudaEvent_t e2 = stage_event(p);
@@ -464,6 +466,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
             xa.part_w0 = w0;
             xa.wp = wp;
             xa.status = p->dev_status;
+            xa.counters = counters;
             xa.order = p->wi_order;
             cudaError_t e;
             // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
@@ -539,25 +542,55 @@ anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_wi
     T *g[4];
     for (int k = 0; k < 4; ++k) g[k] = grids + (size_t)k * p->ws_rhs * gs;
     T *part = reinterpret_cast<T *>(p->part);
+    // FP64 plans run their windows concurrently on the plan's auxiliary streams (forked from the
+    // plan stream and joined back): their stages are long, latency-bound launches per window
+    // (measured: 1.94 -> 1.82 ms at n = 7814, three windows). FP32 stages are single launches over
+    // all windows that already fill the GPU, and forking them measured slower. Stage timing needs
+    // one stream.
+    const bool fork = sizeof(T) == 8 && p->aux[0] && !p->timing && only_window < 0 && p->P >= 2;
     for (int r0 = 0; r0 < nrhs; r0 += chunk) {
         const int nr = std::min(chunk, nrhs - r0);
         const T *vr = v + (size_t)r0 * p->n;
         T *kr = Kv + (size_t)r0 * p->n;
         if (only_window >= 0) {
             // the single window's result goes straight to Kv (part_w0 = only_window)
-            st = matvec_windows<T>(p, vr, nr, only_window, only_window + 1, kr, g, gs);
+            st = matvec_windows<T>(p, vr, nr, only_window, only_window + 1, kr, g, gs, p->stream,
+                                   p->dev_status + 1);
             if (st != ANOVA_OK) return st;
-        } else {
-            st = matvec_windows<T>(p, vr, nr, 0, p->P, part, g, gs);
-            if (st != ANOVA_OK) return st;
-            const long long tot = p->n * nr;
-            const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
-            cudaEvent_t e0 = stage_event(p);
-            k_window_sum<T><<<nb, 256, 0, p->stream>>>(part, kr, p->n, nr, p->P);
-            ANOVA_CUDA_TRY(cudaGetLastError());
-            p->launches += 1;
-            stage_record(p, STAGE_SUM, e0, stage_event(p));
+            continue;
         }
+        if (fork) {
+            // groups (window dimensions) one after another: partial tiles of different
+            // dimensions share workspace under different strides; windows of one group are
+            // independent and run concurrently
+            for (const Group &gr : p->groups) {
+                const int nw = gr.w_end - gr.w_begin;
+                if (nw <= 0) continue;
+                const int na = std::min(nw, kAuxStreams);
+                ANOVA_CUDA_TRY(cudaEventRecord(p->fork_evt, p->stream));
+                for (int k = 0; k < na; ++k) ANOVA_CUDA_TRY(cudaStreamWaitEvent(p->aux[k], p->fork_evt, 0));
+                for (int w = gr.w_begin; w < gr.w_end; ++w) {
+                    const int k = (w - gr.w_begin) % kAuxStreams;
+                    st = matvec_windows<T>(p, vr, nr, w, w + 1, part + (size_t)w * nr * p->n, g, gs, p->aux[k],
+                                           p->dev_status + 1 + kStatusCounters * k);
+                    if (st != ANOVA_OK) return st;
+                }
+                for (int k = 0; k < na; ++k) {
+                    ANOVA_CUDA_TRY(cudaEventRecord(p->join_evt[k], p->aux[k]));
+                    ANOVA_CUDA_TRY(cudaStreamWaitEvent(p->stream, p->join_evt[k], 0));
+                }
+            }
+        } else {
+            st = matvec_windows<T>(p, vr, nr, 0, p->P, part, g, gs, p->stream, p->dev_status + 1);
+            if (st != ANOVA_OK) return st;
+        }
+        const long long tot = p->n * nr;
+        const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
+        cudaEvent_t e0 = stage_event(p);
+        k_window_sum<T><<<nb, 256, 0, p->stream>>>(part, kr, p->n, nr, p->P);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        p->launches += 1;
+        stage_record(p, STAGE_SUM, e0, stage_event(p));
     }
     return ANOVA_OK;
 }

@@ -20,6 +20,9 @@
 #ifndef ANOVA_TC_INTERP_MINB
 #define ANOVA_TC_INTERP_MINB 4  // resident CTAs per SM the tensor-core interpolation is compiled for
 #endif
+#ifndef ANOVA_SPREAD_MINB
+#define ANOVA_SPREAD_MINB 3  // resident CTAs per SM the packed FP32 spread is compiled for
+#endif
 #ifndef ANOVA_SPREAD_UNROLL
 #define ANOVA_SPREAD_UNROLL 8  // points per unrolled group of the packed FP32 spread's inner loop
 #endif
@@ -200,7 +203,7 @@ struct SpreadX2Cfg {
 };
 
 template <int M, int B, int NWARP, int LPP>
-__global__ void __launch_bounds__(NWARP * 32, 3) k_spread3_x2(SpreadArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(SpreadArgs a) {
     using C = SpreadX2Cfg<M, B, NWARP, LPP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
     constexpr int PPS = 32 / LPP;  // points per warp step
@@ -679,6 +682,7 @@ struct InterpWiArgs {
     WinParams wp;
     int *status;             // error bits (tensor-core path: a bounded wait ran out)
     const int *order;        // persistent kernels: work items of each window, largest first
+    int *counters;           // persistent kernels: per-RHS work counters (zeroed before the launch)
 };
 
 template <int M, int B, int NWARP>
@@ -848,7 +852,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     const uint32_t sbase = tc::smem_u32(smem_raw);
     constexpr uint32_t idesc = tc::idesc_tf32(ROWS, C::NCOL);
     const float *fr0 = a.frac, *fr1 = a.frac + a.total, *fr2 = a.frac + 2 * a.total;
-    int *counter = a.status + 1 + r;
+    int *counter = a.counters + r;
     const int nwork = a.wi_end - a.wi_begin;
     // this thread's B entries: row n = t / 2 (a = n / 8, b = n % 8), K half t % 2 (8 values)
     const int bn = t >> 1, bkh = t & 1;

@@ -214,6 +214,14 @@ anova_status ensure_workspace(anova_plan *p, int nrhs) {
 void destroy_plan(anova_plan *p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
+    for (int k = 0; k < 3; ++k) {
+        if (p->aux[k]) {
+            cudaStreamSynchronize(p->aux[k]);
+            cudaStreamDestroy(p->aux[k]);
+        }
+        if (p->join_evt[k]) cudaEventDestroy(p->join_evt[k]);
+    }
+    if (p->fork_evt) cudaEventDestroy(p->fork_evt);
     release_workspace(p);
     void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->bins, p->mbins, p->ftiles, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
@@ -652,8 +660,13 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     }
     if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
-    if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * 32)) != ANOVA_OK) return s;
-    ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * 32, st));
+    if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * 64)) != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * 64, st));
+    for (int k = 0; k < 3; ++k) {
+        ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
+        ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&p->join_evt[k], cudaEventDisableTiming));
+    }
+    ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&p->fork_evt, cudaEventDisableTiming));
     ANOVA_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device));
     std::vector<float> f32;
     if (prec == ANOVA_FP64) {
