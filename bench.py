@@ -313,7 +313,9 @@ def run_ours(args):
     flops = 2.0 * fma_per_pt * n
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (dom_ms / 1000.0) / 1e12
-    traffic = profile_traffic("k_spread_f32_3d_m4" if dominant == "spread" else "k_interp_f32_3d_m4")
+    # the committed DRAM counters are for one right-hand side
+    traffic = (profile_traffic("k_spread_f32_3d_m4" if dominant == "spread" else "k_interp_f32_3d_m4")
+               if nrhs == 1 else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak_tflops, "traffic": traffic,
                 "kernel": "k_%s (FP32, 3-D windows, m=4)" % dominant,

@@ -72,28 +72,6 @@ __global__ void k_saddle_post(const K *__restrict__ Kt, const double *__restrict
         out[i] = y[i] * (double)Kt[i] + theta[i] * x[i] - y[i] * xn;
 }
 
-__global__ void k_scale(const double *__restrict__ a, double s, long long n, double *__restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = s * a[i];
-}
-
-// out = a + sb * b + sc * c
-__global__ void k_lin3(const double *__restrict__ a, const double *__restrict__ b, const double *__restrict__ c,
-                       double sb, double sc, long long n, double *__restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = a[i] + sb * b[i] + sc * c[i];
-}
-
-// w_new = (v - eps w2 - delta w1) / gamma (into w2's buffer); x += phi w_new
-__global__ void k_minres_w(const double *__restrict__ v, double *__restrict__ w2, const double *__restrict__ w1,
-                           double eps, double delta, double inv_gamma, double phi, long long n, double *__restrict__ x) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double w = (v[i] - eps * w2[i] - delta * w1[i]) * inv_gamma;
-        w2[i] = w;
-        x[i] += phi * w;
-    }
-}
-
 __global__ void k_axpy(double a, const double *__restrict__ x, long long n, double *__restrict__ y) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] += a * x[i];
@@ -179,6 +157,135 @@ __global__ void k_objective_partial(const double *__restrict__ al, const double 
 
 int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, kRedBlocks)); }
 
+// ------------------------------------------------------------------ device-resident MINRES
+// The scalar recurrence of MINRES (Paige-Saunders) runs in one-thread kernels on the solver's
+// stream and the vector kernels read their coefficients from device memory, so an iteration needs
+// no host round trip; the host only watches a copy of the `active` flag, a few iterations behind.
+struct MinresState {
+    double beta1, beta, beta_prev, phibar;
+    double c_prev2, s_prev2, c_prev, s_prev;
+    double alpha, beta_next_sq;  // written by the dot products of the iteration
+    double inv_beta, eps, delta, inv_gamma, phi, rtol;
+    int active, do_w, iters, status;  // status: 1 indefinite preconditioner, 2 singular tridiagonal
+    int maxit;
+};
+
+// beta1^2 (the first preconditioned norm) is in beta_next_sq
+__global__ void k_mr_init(MinresState *s, double rtol, int maxit) {
+    const double b2 = s->beta_next_sq;
+    s->rtol = rtol;
+    s->maxit = maxit;
+    s->iters = 0;
+    s->do_w = 0;
+    s->status = 0;
+    s->active = 0;
+    if (b2 < 0.0) {
+        s->status = 1;
+        return;
+    }
+    const double b1 = sqrt(b2);
+    s->beta1 = b1;
+    s->beta = b1;
+    s->beta_prev = 0.0;
+    s->phibar = b1;
+    s->c_prev2 = 1.0;
+    s->s_prev2 = 0.0;
+    s->c_prev = 1.0;
+    s->s_prev = 0.0;
+    s->inv_beta = b1 > 0.0 ? 1.0 / b1 : 0.0;
+    s->active = b1 > 0.0 ? 1 : 0;
+}
+
+// v = y / beta
+__global__ void k_mr_scale(const double *__restrict__ y, const MinresState *__restrict__ s, long long n,
+                           double *__restrict__ v) {
+    if (!s->active) return;
+    const double f = s->inv_beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = f * y[i];
+}
+
+// r_next = A v - (alpha / beta) r_cur - (beta / beta_prev) r_prev
+__global__ void k_mr_lin3(const double *__restrict__ Av, const double *__restrict__ rc, const double *__restrict__ rp,
+                          const MinresState *__restrict__ s, long long n, double *__restrict__ rn) {
+    if (!s->active) return;
+    const double sb = -s->alpha / s->beta, sc = s->beta_prev > 0.0 ? -s->beta / s->beta_prev : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        rn[i] = Av[i] + sb * rc[i] + sc * rp[i];
+}
+
+__device__ void mr_step(MinresState *s) {
+    const double bns = s->beta_next_sq;
+    if (bns < 0.0) {
+        s->status = 1;
+        s->active = 0;
+        return;
+    }
+    const double beta_next = sqrt(bns), beta = s->beta, alpha = s->alpha;
+    const double eps = s->s_prev2 * beta;
+    const double dbar = s->c_prev2 * beta;
+    const double delta = s->c_prev * dbar + s->s_prev * alpha;
+    const double gbar = -s->s_prev * dbar + s->c_prev * alpha;
+    const double gamma = hypot(gbar, beta_next);
+    if (gamma == 0.0) {
+        s->status = 2;
+        s->active = 0;
+        return;
+    }
+    const double c = gbar / gamma, sn = beta_next / gamma;
+    s->phi = c * s->phibar;
+    s->phibar = -sn * s->phibar;
+    s->eps = eps;
+    s->delta = delta;
+    s->inv_gamma = 1.0 / gamma;
+    s->do_w = 1;
+    s->c_prev2 = s->c_prev;
+    s->s_prev2 = s->s_prev;
+    s->c_prev = c;
+    s->s_prev = sn;
+    s->beta_prev = beta;
+    s->beta = beta_next;
+    s->inv_beta = beta_next > 0.0 ? 1.0 / beta_next : 0.0;
+    s->iters += 1;
+    if (fabs(s->phibar) <= s->rtol * s->beta1 || beta_next == 0.0 || s->iters >= s->maxit) s->active = 0;
+}
+
+// the Givens step of the iteration and the convergence test |phibar| <= rtol beta1; inside a
+// graph, `loop` is the handle of the enclosing while node and receives the `active` flag
+__global__ void k_mr_step(MinresState *s, cudaGraphConditionalHandle loop) {
+    s->do_w = 0;
+    if (s->active) mr_step(s);
+    if (loop) cudaGraphSetConditional(loop, s->active ? 1u : 0u);
+}
+
+
+// w_new = (v - eps w2 - delta w1) / gamma; x += phi w_new; then w2 <- w1, w1 <- w_new (the two
+// newest directions stay in fixed buffers)
+__global__ void k_mr_w(const double *__restrict__ v, double *__restrict__ w1, double *__restrict__ w2,
+                       const MinresState *__restrict__ s, long long n, double *__restrict__ x) {
+    if (!s->do_w) return;
+    const double eps = s->eps, delta = s->delta, ig = s->inv_gamma, phi = s->phi;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = w1[i];
+        const double w = (v[i] - eps * w2[i] - delta * a) * ig;
+        w2[i] = a;
+        w1[i] = w;
+        x[i] += phi * w;
+    }
+}
+
+// the Lanczos vectors move down one place: r_prev <- r_cur <- r_next, y_cur <- y_next
+__global__ void k_mr_rotate(double *__restrict__ r_prev, double *__restrict__ r_cur, const double *__restrict__ r_next,
+                            double *__restrict__ y_cur, const double *__restrict__ y_next,
+                            const MinresState *__restrict__ s, long long n) {
+    if (!s->do_w) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        r_prev[i] = r_cur[i];
+        r_cur[i] = r_next[i];
+        y_cur[i] = y_next[i];
+    }
+}
+
 // ------------------------------------------------------------------ solver state
 struct Solver {
     anova_plan *p32 = nullptr, *p64 = nullptr;
@@ -191,6 +298,16 @@ struct Solver {
     float *t32 = nullptr, *k32 = nullptr;
     double *t64 = nullptr, *k64 = nullptr;
     int krylov_total = 0, refine_total = 0, fp64_krylov_total = 0;
+    // device-resident MINRES: scalar state, host copy of its flags, and the FP32 iteration
+    // captured as the body of a conditional while node (built on the first FP32 solve)
+    MinresState *ms = nullptr;
+    int *hflags = nullptr;            // pinned {active, do_w, iters, status}
+    cudaEvent_t ev = nullptr;
+    cudaStream_t cap = nullptr;       // private stream the iteration is captured on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const double *graph_b = nullptr;  // buffers the graph was captured with
+    double *graph_x = nullptr;
 
     anova_status dot(const double *a, const double *b, long long len, double *out) {
         const int nb = blocks_for(len);
@@ -234,66 +351,121 @@ struct Solver {
     }
 };
 
-// Preconditioned MINRES (Paige-Saunders) for A x = b, x0 = 0, vectors of length n + 1.
-anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxit, double *work[10], int *iters,
-                    bool precise = false) {
+// One MINRES iteration on fixed buffers (work[0..8]) and stream st; `loop` is the handle of the
+// enclosing graph while node (0 outside a graph).
+anova_status minres_iteration(Solver &S, double *x, double *work[10], bool precise, cudaStream_t st,
+                              cudaGraphConditionalHandle loop) {
     const long long N1 = S.n + 1;
     const int nb = blocks_for(N1);
     double *r_prev = work[0], *r_cur = work[1], *r_next = work[2], *y_cur = work[3], *y_next = work[4];
     double *v = work[5], *Av = work[6], *w1 = work[7], *w2 = work[8];
+    anova_status s;
+    k_mr_scale<<<nb, 256, 0, st>>>(y_cur, S.ms, N1, v);
+    if ((s = S.apply(v, Av, precise)) != ANOVA_OK) return s;
+    k_dot<<<nb, 256, 0, st>>>(v, Av, N1, S.part);
+    k_sum_to<<<1, 32, 0, st>>>(S.part, nb, 1.0, &S.ms->alpha);
+    k_mr_lin3<<<nb, 256, 0, st>>>(Av, r_cur, r_prev, S.ms, N1, r_next);
+    if ((s = lowrank_apply_impl(S.lr, S.theta, S.y, r_next, y_next)) != ANOVA_OK) return s;
+    k_dot<<<nb, 256, 0, st>>>(r_next, y_next, N1, S.part);
+    k_sum_to<<<1, 32, 0, st>>>(S.part, nb, 1.0, &S.ms->beta_next_sq);
+    k_mr_step<<<1, 1, 0, st>>>(S.ms, loop);
+    k_mr_w<<<nb, 256, 0, st>>>(v, w1, w2, S.ms, N1, x);
+    k_mr_rotate<<<nb, 256, 0, st>>>(r_prev, r_cur, r_next, y_cur, y_next, S.ms, N1);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    return ANOVA_OK;
+}
+
+// Capture the FP32 iteration as the body of a while node whose condition k_mr_step sets. The
+// plans and the solver launch on their `stream` fields, which point at the capture stream while
+// the body is recorded.
+anova_status build_minres_graph(Solver &S, const double *b, double *x, double *work[10]) {
+    if (S.exec) {
+        cudaGraphExecDestroy(S.exec);
+        S.exec = nullptr;
+    }
+    if (S.graph) {
+        cudaGraphDestroy(S.graph);
+        S.graph = nullptr;
+    }
+    if (!S.cap) ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
+    ANOVA_CUDA_TRY(cudaGraphCreate(&S.graph, 0));
+    cudaGraphConditionalHandle loop = 0;
+    ANOVA_CUDA_TRY(cudaGraphConditionalHandleCreate(&loop, S.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ANOVA_CUDA_TRY(cudaGraphAddNode(&node, S.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t saved[3] = {S.st, S.p32->stream, S.lr->plan->stream};
+    S.st = S.p32->stream = S.lr->plan->stream = S.cap;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(S.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    anova_status s = ANOVA_OK;
+    if (e == cudaSuccess) {
+        s = minres_iteration(S, x, work, false, S.cap, loop);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(S.cap, &captured);
+        if (e2 != cudaSuccess && s == ANOVA_OK) s = cuda_fail(e2, "cudaStreamEndCapture");
+    } else {
+        s = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    }
+    S.st = saved[0];
+    S.p32->stream = saved[1];
+    S.lr->plan->stream = saved[2];
+    if (s != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaGraphInstantiate(&S.exec, S.graph, 0));
+    S.graph_b = b;
+    S.graph_x = x;
+    return ANOVA_OK;
+}
+
+// Preconditioned MINRES (Paige-Saunders) for A x = b, x0 = 0, vectors of length n + 1, run on
+// the device (see MinresState). FP32 solves launch one graph whose while node repeats the
+// iteration until the device-side test stops it; FP64 solves (few iterations) run the same
+// iteration from the host, reading the device flags after each one.
+anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxit, double *work[10], int *iters,
+                    bool precise = false) {
+    const long long N1 = S.n + 1;
+    const int nb = blocks_for(N1);
+    double *r_prev = work[0], *r_cur = work[1], *y_cur = work[3], *w1 = work[7], *w2 = work[8];
     cudaStream_t st = S.st;
     anova_status s;
+    if (!precise && (!S.exec || S.graph_b != b || S.graph_x != x)) {
+        // the body's first run inside a graph must not allocate: warm the FP32 operator first
+        if ((s = S.apply(work[5], work[6], false)) != ANOVA_OK) return s;
+        if ((s = build_minres_graph(S, b, x, work)) != ANOVA_OK) return s;
+    }
     ANOVA_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N1, st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(r_prev, 0, sizeof(double) * N1, st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(w1, 0, sizeof(double) * N1, st));
     ANOVA_CUDA_TRY(cudaMemsetAsync(w2, 0, sizeof(double) * N1, st));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(r_cur, b, sizeof(double) * N1, cudaMemcpyDeviceToDevice, st));
     if ((s = lowrank_apply_impl(S.lr, S.theta, S.y, r_cur, y_cur)) != ANOVA_OK) return s;
-    double beta1;
-    if ((s = S.dot(r_cur, y_cur, N1, &beta1)) != ANOVA_OK) return s;
-    *iters = 0;
-    if (beta1 < 0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: preconditioner is not positive definite");
-    beta1 = std::sqrt(beta1);
-    if (beta1 == 0.0) return ANOVA_OK;
-    double beta = beta1, beta_prev = 0.0, phibar = beta1;
-    double c_prev2 = 1.0, s_prev2 = 0.0, c_prev = 1.0, s_prev = 0.0;
-    for (int it = 1; it <= maxit; ++it) {
-        k_scale<<<nb, 256, 0, st>>>(y_cur, 1.0 / beta, N1, v);
-        if ((s = S.apply(v, Av, precise)) != ANOVA_OK) return s;
-        double alpha;
-        if ((s = S.dot(v, Av, N1, &alpha)) != ANOVA_OK) return s;
-        k_lin3<<<nb, 256, 0, st>>>(Av, r_cur, r_prev, -alpha / beta, beta_prev > 0 ? -beta / beta_prev : 0.0, N1, r_next);
-        if ((s = lowrank_apply_impl(S.lr, S.theta, S.y, r_next, y_next)) != ANOVA_OK) return s;
-        double beta_next;
-        if ((s = S.dot(r_next, y_next, N1, &beta_next)) != ANOVA_OK) return s;
-        if (beta_next < 0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: preconditioner is not positive definite");
-        beta_next = std::sqrt(beta_next);
-        const double eps = s_prev2 * beta;
-        const double dbar = c_prev2 * beta;
-        const double delta = c_prev * dbar + s_prev * alpha;
-        const double gbar = -s_prev * dbar + c_prev * alpha;
-        double gamma = std::hypot(gbar, beta_next);
-        if (gamma == 0.0) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: singular tridiagonal");
-        const double c = gbar / gamma, sn = beta_next / gamma;
-        const double phi = c * phibar;
-        phibar = -sn * phibar;
-        k_minres_w<<<nb, 256, 0, st>>>(v, w2, w1, eps, delta, 1.0 / gamma, phi, N1, x);
-        ANOVA_CUDA_TRY(cudaGetLastError());
-        std::swap(w1, w2);  // w1 <- newest w, w2 <- previous
-        c_prev2 = c_prev;
-        s_prev2 = s_prev;
-        c_prev = c;
-        s_prev = sn;
-        std::swap(r_prev, r_cur);
-        std::swap(r_cur, r_next);
-        std::swap(y_cur, y_next);
-        beta_prev = beta;
-        beta = beta_next;
-        *iters = it;
-        if (std::fabs(phibar) <= rtol * beta1 || beta == 0.0) break;
+    k_dot<<<nb, 256, 0, st>>>(r_cur, y_cur, N1, S.part);
+    k_sum_to<<<1, 32, 0, st>>>(S.part, nb, 1.0, &S.ms->beta_next_sq);
+    k_mr_init<<<1, 1, 0, st>>>(S.ms, rtol, maxit);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    if (!precise) {
+        ANOVA_CUDA_TRY(cudaGraphLaunch(S.exec, st));
+    } else {
+        for (int it = 1; it <= maxit; ++it) {
+            if ((s = minres_iteration(S, x, work, true, st, 0)) != ANOVA_OK) return s;
+            ANOVA_CUDA_TRY(cudaMemcpyAsync(S.hflags, &S.ms->active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            ANOVA_CUDA_TRY(cudaEventRecord(S.ev, st));
+            ANOVA_CUDA_TRY(cudaEventSynchronize(S.ev));
+            if (!S.hflags[0]) break;
+        }
     }
+    int fin[4];
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(fin, &S.ms->active, sizeof(fin), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    *iters = fin[2];
     if (precise) S.fp64_krylov_total += *iters;
     else S.krylov_total += *iters;
+    if (fin[3] == 1) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: preconditioner is not positive definite");
+    if (fin[3] == 2) return fail(ANOVA_ERR_BREAKDOWN, "MINRES: singular tridiagonal");
     return ANOVA_OK;
 }
 
@@ -469,7 +641,23 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                   dalloc(sizeof(float) * n, (void **)&S.t32) && dalloc(sizeof(float) * n, (void **)&S.k32) &&
                   dalloc(sizeof(double) * n, (void **)&S.t64) && dalloc(sizeof(double) * n, (void **)&S.k64);
         for (int k = 0; k < 10 && ok; ++k) ok = dalloc(sizeof(double) * N1, (void **)&work[k]);
+        ok = ok && dalloc(sizeof(MinresState), (void **)&S.ms);
         if (!ok) return fail(ANOVA_ERR_OOM, "solver allocation failed");
+        struct HostRes {
+            Solver &s;
+            ~HostRes() {
+                if (s.exec) cudaGraphExecDestroy(s.exec);
+                if (s.graph) cudaGraphDestroy(s.graph);
+                if (s.cap) {
+                    cudaStreamSynchronize(s.cap);
+                    cudaStreamDestroy(s.cap);
+                }
+                if (s.hflags) cudaFreeHost(s.hflags);
+                if (s.ev) cudaEventDestroy(s.ev);
+            }
+        } host_res{S};
+        ANOVA_CUDA_TRY(cudaHostAlloc((void **)&S.hflags, sizeof(int) * 4, cudaHostAllocDefault));
+        ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
         S.y = dy;
         S.theta = dth;
         ANOVA_CUDA_TRY(cudaMemcpyAsync(dy, yh, sizeof(double) * n, cudaMemcpyHostToDevice, st));
