@@ -165,6 +165,20 @@ anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void 
  */
 anova_status anova_spread_grid_noalloc(anova_plan_t plan, int l, const void *v, void *grid);
 
+/*
+ * anova_cross_matvec -- the product with targets distinct from the sources, as in evaluating the
+ * trained decision function f(x) = sum_i alpha_i y_i K(x_i, x) + b at new points (Sec. 6):
+ *   f_j = sum_l eta_l sum_i w_i exp(-||t_j^{W_l} - s_i^{W_l}||^2 / ell_l^2),   j < n_target,
+ * by NFFT fast summation: the sources are spread with `source`'s plan, each window's grid is
+ * convolved in full (FFT, scaling, inverse FFT), and the result is interpolated at the targets
+ * with `target`'s plan. Both plans must be built from the same windows, N, m, precision and
+ * per-window ell_l, eta_l (otherwise ANOVA_ERR_INVALID_ARG); their points (and counts) differ.
+ * w: device, n_source values of the plans' precision; f: device, n_target values (overwritten).
+ * Allocates two grids of scratch for the call and synchronises both plans' streams; the plans'
+ * own matvec state is not touched.
+ */
+anova_status anova_cross_matvec(anova_plan_t source, anova_plan_t target, const void *w, void *f);
+
 /* Plan facts. Any output pointer may be NULL. device_bytes = device memory the plan holds. */
 anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
                              int64_t *device_bytes);

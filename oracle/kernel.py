@@ -107,3 +107,17 @@ def window_kernel_matrix(X, window, ell):
         diff = X[j, feats][None, :] - X[:, feats]
         K[j] = np.exp(-np.sum(diff * diff, axis=1) / ell ** 2)
     return K
+
+
+def anova_cross_matvec(Xs, Xt, windows, ell, w, eta=None):
+    """Direct FP64 sum with targets distinct from the sources, as in evaluating the decision
+    function at new points (Sec. 6): f_j = sum_i w_i kappa(s_i, t_j). Written as the square
+    matvec on the stacked point set [sources; targets] with zero weights on the targets, read
+    at the target rows, so it is the pinned definition above and nothing else."""
+    Xs = np.asarray(Xs, dtype=np.float64)
+    Xt = np.asarray(Xt, dtype=np.float64)
+    ns = Xs.shape[0]
+    X = np.vstack([Xs, Xt])
+    v = np.concatenate([np.asarray(w, dtype=np.float64), np.zeros(Xt.shape[0])])
+    rows = np.arange(ns, ns + Xt.shape[0])
+    return anova_matvec(X, windows, ell, v, rows=rows, eta=eta)

@@ -66,6 +66,7 @@ _SIGNATURES = {
                                  ctypes.POINTER(_c_int), _lp]),
     "anova_plan_destroy": (None, [_vp]),
     "anova_plan_check": (_c_int, [_vp]),
+    "anova_cross_matvec": (_c_int, [_vp, _vp, _vp, _vp]),
     "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
     "anova_kernel_coeffs": (_c_int, [_c_dbl, _c_int, _dp]),
@@ -253,6 +254,11 @@ def anova_plan_info(plan):
     _check(lib().anova_plan_info(plan.handle, ctypes.byref(n), ctypes.byref(P), ctypes.byref(nos),
                                  ctypes.byref(fl), ctypes.byref(nb)))
     return dict(n=n.value, P=P.value, n_os=nos.value, flags=fl.value, device_bytes=nb.value)
+
+
+def anova_cross_matvec(source, target, w, f):
+    """f (device, target points) = sum over windows and sources of w_i K(t_j, s_i)."""
+    _check(lib().anova_cross_matvec(source.handle, target.handle, _dev_ptr(w), _dev_ptr(f)))
 
 
 def anova_plan_check(plan):

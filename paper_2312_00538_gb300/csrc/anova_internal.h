@@ -159,4 +159,6 @@ template <typename T>
 anova_status run_conv_grid_t(anova_plan *p, int w, const void *in, void *out);
 template <typename T>
 anova_status run_interp_grid_t(anova_plan *p, int w, const void *grid, void *f);
+template <typename T>
+anova_status run_cross_matvec_t(anova_plan *src, anova_plan *tgt, const void *w, void *f);
 }  // namespace anova

@@ -231,6 +231,25 @@ anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, i
     return ANOVA_OK;
 }
 
+anova_status anova_cross_matvec(anova_plan_t source, anova_plan_t target, const void *w, void *f) {
+    return guarded([&]() -> anova_status {
+        if (!source || !target) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!w || !f) return fail(ANOVA_ERR_INVALID_ARG, "w or f is NULL");
+        if (source->device != target->device) return fail(ANOVA_ERR_INVALID_ARG, "plans on different devices");
+        if (source->prec != target->prec || source->N != target->N || source->m != target->m ||
+            source->P != target->P || source->user_to_internal != target->user_to_internal)
+            return fail(ANOVA_ERR_INVALID_ARG, "source and target plans differ in precision, N, m or windows");
+        for (int k = 0; k < source->P; ++k) {
+            const WindowInfo &a = source->win[k], &b = target->win[k];
+            if (a.dw != b.dw || a.ell != b.ell || a.eta != b.eta)
+                return fail(ANOVA_ERR_INVALID_ARG, "source and target plans differ in a window's dimension, ell or eta");
+        }
+        DeviceGuard g(source->device);
+        if (source->prec == ANOVA_FP64) return run_cross_matvec_t<double>(source, target, w, f);
+        return run_cross_matvec_t<float>(source, target, w, f);
+    });
+}
+
 anova_status anova_plan_check(anova_plan_t plan) {
     return guarded([&]() -> anova_status {
         if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");

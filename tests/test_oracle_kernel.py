@@ -95,3 +95,23 @@ def test_matches_pairwise_loop():
     Kl = ok.window_kernel_matrix(X, [0, 1, 2], 0.45)
     assert np.allclose(ok.anova_matvec(X, np.array([[0, 1, 2]]), 0.45, v), Kl @ v,
                        rtol=1e-13, atol=1e-13)
+
+
+def test_cross_matvec_by_brute_force():
+    """Targets distinct from sources: against a NumPy double loop over both sets; with the targets
+    equal to the sources it is the square matvec."""
+    rng = np.random.default_rng(77)
+    Xs = rng.uniform(-0.2, 0.2, size=(30, 4))
+    Xt = rng.uniform(-0.2, 0.2, size=(17, 4))
+    W = np.array([[0, 1, -1], [2, 3, -1], [1, -1, -1]])
+    w = rng.standard_normal(30)
+    ref = np.zeros(17)
+    for j in range(17):
+        for i in range(30):
+            for win in W:
+                f = [k for k in win if k >= 0]
+                ref[j] += w[i] * np.exp(-np.sum((Xt[j, f] - Xs[i, f]) ** 2) / 0.7 ** 2)
+    got = ok.anova_cross_matvec(Xs, Xt, W, 0.7, w)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert np.allclose(ok.anova_cross_matvec(Xs, Xs, W, 0.7, w), ok.anova_matvec(Xs, W, 0.7, w),
+                       rtol=1e-14, atol=1e-14)
