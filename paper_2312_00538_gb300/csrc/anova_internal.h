@@ -16,7 +16,10 @@ constexpr double kOversampling = 2.0;  // n_os = 2N
 constexpr double kEpsB = 0.1;          // kernel fit on |t| <= 1/2 - eps_B
 constexpr double kBoxHalf = 0.2;       // points in [-0.2, 0.2]
 constexpr int kSegMax = 256;           // points per segment (one cell, split at this size)
-constexpr int kWiMax = 2048;           // points per spread work item (one bin)
+#ifndef ANOVA_WI_MAX
+#define ANOVA_WI_MAX 2048
+#endif
+constexpr int kWiMax = ANOVA_WI_MAX;  // points per spread work item (at most)
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
