@@ -132,3 +132,57 @@ def blockdiag_apply(Zt, theta, y, g, s):
     out[:n] = woodbury_apply(Zt, theta, y, g[:n])
     out[n] = g[n] / s
     return out
+
+
+_GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed, j):
+    """Output number j (0-based) of SplitMix64 started at `seed` (Steele, Lea and Flood, 2014; the
+    generator behind Java's SplittableRandom): the state seed + (j + 1) * 0x9E3779B97F4A7C15 passed
+    through the generator's 64-bit finaliser."""
+    z = (int(seed) + (int(j) + 1) * _GOLDEN_GAMMA) & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def uniform01(seed, j):
+    """The top 53 bits of splitmix64(seed, j) as a double in [0, 1)."""
+    return (splitmix64(seed, j) >> 11) * 2.0 ** -53
+
+
+def _rp_draw(seed):
+    def draw(d, j):
+        c = np.cumsum(np.maximum(d, 0.0))
+        return int(np.searchsorted(c, uniform01(seed, j) * c[-1], side="right"))
+    return draw
+
+
+def rp_cholesky(K, k, seed, err_tol=0.0, pick=None):
+    """Randomly pivoted Cholesky (Sec. 4, the variant after Algorithm 2): every pivot is drawn with
+    probability proportional to the current residual diagonal d. The draw of step j is the first
+    index s (in index order) with cumsum(max(d, 0))[s] > u_j * sum(max(d, 0)), u_j =
+    uniform01(seed, j). Columns as in Algorithm 2: L(:, j) = (K(:, s) - L(:, :j) L(s, :j)^T) /
+    sqrt(d_s), d -= L(:, j)^2. Stops at rank k or, as the greedy version, when max(d) <= err_tol *
+    max(diag K). Returns (L, piv) with K ~ L L^T in the original row order. `pick(d, j)` replaces
+    the draw (tests use the arg-max to recover the greedy Algorithm 2)."""
+    pick = _rp_draw(seed) if pick is None else pick
+    K = np.asarray(K, dtype=np.float64)
+    n = K.shape[0]
+    d = np.diag(K).copy()
+    dmax0 = float(np.max(d)) if n else 0.0
+    L = np.zeros((n, k))
+    piv = []
+    for j in range(min(k, n)):
+        dm = float(np.max(d))
+        if not (dm > 0.0) or dm <= err_tol * dmax0:
+            break
+        s = min(pick(d, j), n - 1)
+        col = K[:, s] - L[:, :j] @ L[s, :j]
+        L[:, j] = col / np.sqrt(d[s])
+        d = d - L[:, j] ** 2
+        piv.append(s)
+    r = len(piv)
+    return L[:, :r].copy(), np.array(piv, dtype=np.int64)

@@ -139,3 +139,58 @@ def test_minres_with_low_rank_preconditioner():
     xd = np.linalg.solve(Acal, b)
     assert info["converged"]
     assert np.allclose(x, xd, rtol=1e-7, atol=1e-7 * np.max(np.abs(xd)))
+
+
+def test_splitmix64_reference_outputs():
+    """The first outputs of SplitMix64 started at 0, as published with the generator."""
+    assert [op.splitmix64(0, j) for j in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                       0x06C45D188009454F]
+    u = np.array([op.uniform01(123, j) for j in range(20000)])
+    assert 0.0 <= u.min() and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.005
+
+
+def test_rp_cholesky_full_rank_and_triangular_structure():
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-0.2, 0.2, size=(24, 3))
+    K = ok.anova_kernel_matrix(X, np.array([[0, 1, 2]]), 0.3)
+    L, piv = op.rp_cholesky(K, 24, seed=7)
+    assert len(set(piv.tolist())) == len(piv)                       # no pivot twice
+    assert np.allclose(L @ L.T, K, atol=1e-10 * np.max(K)) or len(piv) < 24
+    # in pivot order L is lower triangular
+    Lp = L[piv, :]
+    assert np.max(np.abs(np.triu(Lp, 1))) <= 1e-12
+    # at the rank it reached, the residual diagonal is what the factor leaves
+    assert np.allclose(np.diag(K - L @ L.T), np.maximum(np.diag(K) - np.sum(L ** 2, axis=1), 0.0),
+                       atol=1e-10)
+
+
+def test_rp_cholesky_draws_in_proportion_to_the_residual_diagonal():
+    """Over many seeds the first pivot is uniform (equal diagonal) and the second pivot, given the
+    first, follows the residual diagonal after one step."""
+    K = np.array([[1.0, 0.9, 0.1, 0.0], [0.9, 1.0, 0.2, 0.1], [0.1, 0.2, 1.0, 0.5], [0.0, 0.1, 0.5, 1.0]])
+    first = np.zeros(4)
+    second_after0 = np.zeros(4)
+    for seed in range(4000):
+        _, piv = op.rp_cholesky(K, 2, seed=seed)
+        first[piv[0]] += 1
+        if piv[0] == 0:
+            second_after0[piv[1]] += 1
+    assert np.all(np.abs(first / 4000 - 0.25) < 4 * np.sqrt(0.25 * 0.75 / 4000))
+    d1 = 1.0 - K[:, 0] ** 2                      # residual diagonal after pivot 0
+    p = d1 / d1.sum()
+    m = second_after0.sum()
+    assert second_after0[0] == 0
+    assert np.all(np.abs(second_after0 / m - p) < 4 * np.sqrt(p * (1 - p) / m) + 1e-12)
+
+
+def test_rp_cholesky_with_argmax_draws_is_algorithm_2():
+    """Replacing the draw by the first arg-max of the residual diagonal gives the greedy factor of
+    Algorithm 2 (pivots and columns): the column formula is Algorithm 2's."""
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-0.2, 0.2, size=(40, 3))
+    K = ok.anova_kernel_matrix(X, np.array([[0, 1, 2]]), 0.5)
+    Lg, pg = op.pivoted_cholesky(K, 12)
+    L, piv = op.rp_cholesky(K, 12, seed=0, pick=lambda d, j: int(np.argmax(d)))
+    assert piv.tolist() == pg.tolist()
+    assert np.allclose(L, Lg, atol=1e-12)
