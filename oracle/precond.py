@@ -164,7 +164,8 @@ def rp_cholesky(K, k, seed, err_tol=0.0, pick=None):
     """Randomly pivoted Cholesky (Sec. 4, the variant after Algorithm 2): every pivot is drawn with
     probability proportional to the current residual diagonal d. The draw of step j is the first
     index s (in index order) with cumsum(max(d, 0))[s] > u_j * sum(max(d, 0)), u_j =
-    uniform01(seed, j). Columns as in Algorithm 2: L(:, j) = (K(:, s) - L(:, :j) L(s, :j)^T) /
+    uniform01(seed, j); an entry with d <= 0 is never drawn (the index moves back to the last
+    positive entry). Columns as in Algorithm 2: L(:, j) = (K(:, s) - L(:, :j) L(s, :j)^T) /
     sqrt(d_s), d -= L(:, j)^2. Stops at rank k or, as the greedy version, when max(d) <= err_tol *
     max(diag K). Returns (L, piv) with K ~ L L^T in the original row order. `pick(d, j)` replaces
     the draw (tests use the arg-max to recover the greedy Algorithm 2)."""
@@ -180,6 +181,10 @@ def rp_cholesky(K, k, seed, err_tol=0.0, pick=None):
         if not (dm > 0.0) or dm <= err_tol * dmax0:
             break
         s = min(pick(d, j), n - 1)
+        # entries with zero weight are never drawn: a target that rounding puts at or past the end
+        # of the cumulative sum moves to the last positive entry before it
+        while s > 0 and not d[s] > 0.0:
+            s -= 1
         col = K[:, s] - L[:, :j] @ L[s, :j]
         L[:, j] = col / np.sqrt(d[s])
         d = d - L[:, j] ** 2
