@@ -67,7 +67,8 @@ enum {
 /* Low-rank preconditioner kinds (lowrank_precond_build `kind`). */
 enum {
     PCHOL_GREEDY = 0, /* Algorithm 2: greedy pivoted Cholesky (Sec. 4) */
-    NYSTROM = 1       /* Nystrom K ~ (KQ)(Q^T K Q)^{-1}(KQ)^T with Q = pivoted columns (Sec. 4) */
+    NYSTROM = 1,      /* Nystrom K ~ (KQ)(Q^T K Q)^{-1}(KQ)^T with Q = pivoted columns (Sec. 4) */
+    PCHOL_RANDOM = 2  /* randomly pivoted Cholesky: pivots drawn by the residual diagonal (Sec. 4) */
 };
 
 /*

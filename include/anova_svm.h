@@ -33,7 +33,12 @@ extern "C" {
  *   kind = NYSTROM: K(:,S) K(S,S)^{-1} K(S,:) on the pivot set S of the greedy pass, with the
  *          core K(S,S) factored as L D L^T and entries of D below 1e-10 max D set to that value
  *          (Sec. 4).
- * seed is reserved for randomised variants and ignored by these two kinds.
+ *   kind = PCHOL_RANDOM: randomly pivoted Cholesky (Sec. 4, after Algorithm 2): pivot j is drawn
+ *          with probability proportional to the residual diagonal d, as the first index s (in
+ *          point order) with cumsum(max(d, 0))[s] > u_j sum(max(d, 0)), where u_j is output j of
+ *          SplitMix64 started at `seed` (state seed + (j + 1) 0x9E3779B97F4A7C15 through its
+ *          finaliser), top 53 bits scaled to [0, 1). Columns and stop rule as PCHOL_GREEDY.
+ * seed is used by PCHOL_RANDOM only.
  * The plan must outlive the preconditioner. Requires eta_l >= 0 (K positive semidefinite).
  * Errors: INVALID_ARG (r outside [1, 1024], bad kind, negative eta), OOM, CUDA.
  */
@@ -88,7 +93,7 @@ typedef struct {
     int refine_max;          /* FP64 refinement passes per Newton solve (default 4); when the
                                 FP32-operator passes stop reducing the FP64 residual, the solve
                                 finishes with MINRES on the FP64 operator */
-    int precond;             /* PCHOL_GREEDY or NYSTROM */
+    int precond;             /* PCHOL_GREEDY, NYSTROM or PCHOL_RANDOM (with `seed`) */
     int rank;                /* preconditioner rank (default 200, at most n) */
     double err_tol;          /* pivoted-Cholesky tolerance (Table 1: 1e-5) */
     uint64_t seed;

@@ -32,6 +32,7 @@ ANOVA_INTERP_TENSOR = 2
 ANOVA_INTERP_SIMT = 4
 PCHOL_GREEDY = 0
 NYSTROM = 1
+PCHOL_RANDOM = 2
 
 
 class AnovaError(RuntimeError):

@@ -127,6 +127,74 @@ __global__ void k_pchol_pick(int j, int nparts, const ValIdx *__restrict__ parti
     }
 }
 
+// ------------------------------------------------------------------ randomly pivoted Cholesky
+// Output j of SplitMix64 started at `seed` (Steele, Lea and Flood, 2014): the state
+// seed + (j + 1) * 0x9E3779B97F4A7C15 through the generator's finaliser; top 53 bits in [0, 1).
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, long long j) {
+    unsigned long long z = seed + (unsigned long long)(j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// sums of max(d, 0) over contiguous chunks [b chunk, (b + 1) chunk), in a fixed order
+__global__ void __launch_bounds__(256) k_rp_chunk_sums(const double *__restrict__ d, long long n, long long chunk,
+                                                       const int *__restrict__ stop, double *__restrict__ part) {
+    __shared__ double ws[8];
+    if (*stop >= 0) return;
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    double s = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += fmax(d[i], 0.0);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Pivot j + 1 (j = -1: the first) drawn in proportion to the residual diagonal: the first index s
+// with cumsum(max(d, 0))[s] > u_{j+1} * sum. Stop rule as the greedy pick (rank, or the largest
+// residual diagonal <= thresh); `argmax` holds the column kernel's per-block maxima (nargmax of
+// them; none before the first column, when the largest entry is dmax0).
+__global__ void k_rp_pick(int j, unsigned long long seed, const double *__restrict__ d, long long n,
+                          long long chunk, int nchunks, const double *__restrict__ part,
+                          const ValIdx *__restrict__ argmax, int nargmax, double dmax0, long long *piv,
+                          double *dpiv, int *stop, int rmax, double thresh) {
+    if (threadIdx.x != 0 || *stop >= 0) return;
+    double dmax = dmax0;
+    if (nargmax > 0) {
+        dmax = -INFINITY;
+        for (int t = 0; t < nargmax; ++t) dmax = fmax(dmax, argmax[t].v);
+    }
+    if (j + 1 >= rmax || !(dmax > thresh) || !(dmax > 0.0)) {
+        *stop = j + 1;
+        return;
+    }
+    double total = 0.0;
+    for (int b = 0; b < nchunks; ++b) total += part[b];
+    const double target = splitmix_uniform(seed, j + 1) * total;
+    double run = 0.0;
+    int b = 0;
+    while (b < nchunks - 1 && run + part[b] <= target) run += part[b++];
+    const long long lo = (long long)b * chunk, hi = min(n, lo + chunk);
+    long long s = hi - 1;
+    for (long long i = lo; i < hi; ++i) {
+        run += fmax(d[i], 0.0);
+        if (run > target) {
+            s = i;
+            break;
+        }
+    }
+    // a draw that lands on a zero residual (rounding at a chunk edge) moves to the last positive one
+    while (s > 0 && !(d[s] > 0.0)) --s;
+    piv[j + 1] = s;
+    dpiv[j + 1] = d[s];
+}
+
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, long long cnt) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
@@ -448,12 +516,12 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
     if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
-    if (kind != PCHOL_GREEDY && kind != NYSTROM) return fail(ANOVA_ERR_INVALID_ARG, "unknown preconditioner kind");
+    if (kind != PCHOL_GREEDY && kind != NYSTROM && kind != PCHOL_RANDOM)
+        return fail(ANOVA_ERR_INVALID_ARG, "unknown preconditioner kind");
     if (r < 1 || r > 1024) return fail(ANOVA_ERR_INVALID_ARG, "rank must be in [1, 1024]");
     if (!(err_tol >= 0.0) || !std::isfinite(err_tol)) return fail(ANOVA_ERR_INVALID_ARG, "err_tol must be >= 0");
     for (int w = 0; w < p->P; ++w)
         if (p->win[w].eta < 0) return fail(ANOVA_ERR_INVALID_ARG, "low-rank factors need eta_l >= 0 (K must be PSD)");
-    (void)seed;
     const long long n = p->n;
     r = (int)std::min<long long>(r, n);
     lowrank *lr = new (std::nothrow) lowrank();
@@ -487,12 +555,36 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
     ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->dpiv, &diag, sizeof(double), cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->stop, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
     const double thresh = err_tol * diag;
+    // randomly pivoted: contiguous chunks of the residual diagonal for the draws
+    const bool random = kind == PCHOL_RANDOM;
+    const int rp_chunks = (int)std::min<long long>(1024, std::max<long long>(1, (n + 1023) / 1024));
+    const long long rp_chunk = (n + rp_chunks - 1) / rp_chunks;
+    double *rp_part = nullptr;
+    if (random) {
+        if ((e = cudaMalloc(&rp_part, sizeof(double) * rp_chunks)) != cudaSuccess)
+            return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+        k_rp_chunk_sums<<<rp_chunks, 256, 0, st>>>(lr->d, n, rp_chunk, lr->stop, rp_part);
+        k_rp_pick<<<1, 32, 0, st>>>(-1, seed, lr->d, n, rp_chunk, rp_chunks, rp_part, nullptr, 0, diag,
+                                    (long long *)lr->piv_dev, lr->dpiv, lr->stop, r + 1, thresh);
+    }
+    struct FreeDev {
+        void *p;
+        ~FreeDev() {
+            if (p) cudaFree(p);
+        }
+    } free_rp{rp_part};
     for (int j = 0; j < r; ++j) {
         k_pchol_column<<<nb, 256, sizeof(double) * std::max(1, j), st>>>(
             j, p->xw, n, kp, lr->L64, lr->d, (const long long *)lr->piv_dev, lr->dpiv, lr->stop,
             (ValIdx *)lr->partial);
-        k_pchol_pick<<<1, 32, 0, st>>>(j, nb, (const ValIdx *)lr->partial, (long long *)lr->piv_dev,
-                                       lr->dpiv, lr->stop, r, thresh);
+        if (random) {
+            k_rp_chunk_sums<<<rp_chunks, 256, 0, st>>>(lr->d, n, rp_chunk, lr->stop, rp_part);
+            k_rp_pick<<<1, 32, 0, st>>>(j, seed, lr->d, n, rp_chunk, rp_chunks, rp_part, (const ValIdx *)lr->partial,
+                                        nb, diag, (long long *)lr->piv_dev, lr->dpiv, lr->stop, r, thresh);
+        } else {
+            k_pchol_pick<<<1, 32, 0, st>>>(j, nb, (const ValIdx *)lr->partial, (long long *)lr->piv_dev,
+                                           lr->dpiv, lr->stop, r, thresh);
+        }
     }
     ANOVA_CUDA_TRY(cudaGetLastError());
     int rank = 0;

@@ -78,3 +78,24 @@ def test_large_C_workload3_like(env, C):
     d_gpu = oi.dual_objective(K, y, alpha)
     d_ref = oi.dual_objective(K, y, ref["alpha"])
     assert abs(d_gpu - d_ref) <= 1e-6 * abs(d_ref)
+
+
+@pytest.mark.parametrize("kind", ["random", "nystrom"])
+def test_other_preconditioners_reach_the_same_optimum(env, kind):
+    """The optimum does not depend on the preconditioner: randomly pivoted Cholesky and Nystrom
+    reach the dense-KKT oracle's dual objective on workload 1 (only iteration counts differ)."""
+    torch, ab = env
+    cfg = config1()
+    X, y, W, C = cfg["X"], cfg["y"], cfg["windows"], cfg["C"]
+    o = ab.svm_opts_default()
+    o.rank = 200
+    o.krylov_tol = 1e-8
+    o.max_iter = 100
+    o.precond = ab.PCHOL_RANDOM if kind == "random" else ab.NYSTROM
+    o.seed = 2023
+    alpha, b, st, status = ab.svm_ipm_solve(X, y, C, 1e-6, opts=o, windows=W)
+    assert status == ab.ANOVA_OK
+    K = ok.anova_kernel_matrix(X, W, cfg["sigma"])
+    ref = oi.ipm_dense(K, y, C, tol=1e-9, max_iter=200)
+    d_ref = oi.dual_objective(K, y, ref["alpha"])
+    assert abs(oi.dual_objective(K, y, alpha) - d_ref) <= 1e-6 * abs(d_ref)

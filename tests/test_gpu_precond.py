@@ -100,3 +100,25 @@ def test_woodbury_block_preconditioner(env):
     # and against the dense inverse of A^ with the same factor
     dense = np.linalg.solve(op.dense_Ahat(L32, theta, y), g[:500])
     assert np.allclose(got[:500], dense, rtol=1e-7, atol=1e-9 * np.max(np.abs(dense)))
+
+
+@pytest.mark.parametrize("seed", [0, 12345, 2 ** 63 + 7])
+def test_randomly_pivoted_cholesky_matches_oracle(env, seed):
+    """Same SplitMix64 draws on both sides: identical pivots and the same factor."""
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=400, seed=3)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_RANDOM, 30, 0.0, seed=seed)
+    L, piv = _factor(torch, ab, lr, 400)
+    Lo, pivo = op.rp_cholesky(K, 30, seed=seed)
+    assert np.array_equal(piv, pivo)
+    assert np.allclose(L, Lo, rtol=0, atol=1e-10)
+
+
+def test_randomly_pivoted_cholesky_err_tol_stop(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=200, d=3, ell=2.0)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_RANDOM, 200, 1e-5, seed=99)
+    L, piv = _factor(torch, ab, lr, 200)
+    Lo, pivo = op.rp_cholesky(K, 200, seed=99, err_tol=1e-5)
+    assert np.array_equal(piv, pivo)
+    assert np.max(np.diag(K - L @ L.T)) <= 1e-5 * np.max(np.diag(K)) + 1e-13
