@@ -75,6 +75,16 @@ enum {
     SVM_STOP_ALG1 = 1  /* Algorithm 1's test: mu and both relative infeasibilities below tol */
 };
 
+/* Krylov method of the Newton solves (Sec. 5). Both run on the FP32 operator with FP64
+ * refinement; the FP64 fallback solve is MINRES either way.
+ *   SVM_KRYLOV_MINRES: MINRES with the SPD block preconditioner blockdiag(A^, y^T A^{-1} y).
+ *   SVM_KRYLOV_GMRES: right-preconditioned GMRES with the paper's P = [[A^, 0], [-y^T, -1]],
+ *     krylov_max Arnoldi steps without restart (basis of (krylov_max + 1) (n + 1) doubles). */
+enum {
+    SVM_KRYLOV_MINRES = 0,
+    SVM_KRYLOV_GMRES = 1
+};
+
 /* Barrier schedules (Sec. 2: mu is reduced by a constant sigma or by a sigma_it per iteration). */
 enum {
     SVM_SIGMA_CONSTANT = 0,  /* mu <- sigma mu */
@@ -104,6 +114,7 @@ typedef struct {
     int N_precise, m_precise;/* FP64 plan for residuals and objectives (default 64, 6) */
     int scale_features;      /* 1: min-max scale every feature into [-0.2, 0.2] first */
     void *cuda_stream;
+    int krylov;              /* SVM_KRYLOV_MINRES (default) or SVM_KRYLOV_GMRES */
 } svm_opts;
 
 typedef struct {

@@ -33,6 +33,8 @@ ANOVA_INTERP_SIMT = 4
 PCHOL_GREEDY = 0
 NYSTROM = 1
 PCHOL_RANDOM = 2
+SVM_KRYLOV_MINRES = 0
+SVM_KRYLOV_GMRES = 1
 
 
 class AnovaError(RuntimeError):
@@ -323,7 +325,7 @@ class svm_opts(ctypes.Structure):
                 ("windows", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int),
                 ("N", ctypes.c_int), ("m", ctypes.c_int), ("N_precise", ctypes.c_int),
                 ("m_precise", ctypes.c_int), ("scale_features", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("krylov", ctypes.c_int)]
 
 
 class svm_stats(ctypes.Structure):

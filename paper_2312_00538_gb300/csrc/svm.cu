@@ -286,6 +286,178 @@ __global__ void k_mr_rotate(double *__restrict__ r_prev, double *__restrict__ r_
     }
 }
 
+// ------------------------------------------------------------------ device-resident GMRES
+// Right-preconditioned GMRES (Saad and Schultz) with the paper's block-triangular P (Sec. 5),
+// no restart inside a call. Arnoldi with classical Gram-Schmidt done twice (each pass: all dot
+// products in one launch, then one update), Givens rotations in a one-thread kernel; the basis
+// column j, the Hessenberg matrix and the rotations live in device memory and the kernels read j
+// from there, so the iteration is a fixed launch sequence (captured as a graph while loop).
+struct GmresState {
+    double beta, rtol, resid, hnext;
+    int j, m, active, status;
+};
+constexpr int kGsBlocks = 64;  // row blocks of the Gram-Schmidt dot products
+
+__global__ void k_gm_init(GmresState *s, const double *__restrict__ bnorm2, double rtol, int m, double *g) {
+    const double b = sqrt(fmax(*bnorm2, 0.0));
+    s->beta = b;
+    s->rtol = rtol;
+    s->resid = b;
+    s->m = m;
+    s->j = 0;
+    s->status = 0;
+    s->active = b > 0.0 ? 1 : 0;
+    g[0] = b;
+}
+
+// V(:, 0) = b / beta
+__global__ void k_gm_first(const double *__restrict__ b, const GmresState *__restrict__ s, long long n,
+                           double *__restrict__ V0) {
+    if (!s->active) return;
+    const double f = 1.0 / s->beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        V0[i] = f * b[i];
+}
+
+// vj = V(:, j)
+__global__ void k_gm_col(const double *__restrict__ V, const GmresState *__restrict__ s, long long n,
+                         double *__restrict__ vj) {
+    if (!s->active) return;
+    const double *c = V + (size_t)s->j * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        vj[i] = c[i];
+}
+
+// the last entry of P^{-1} g: x_n = -(g_n + y^T x[0:n]) with y^T x[0:n] in `part`
+__global__ void k_tri_last(const double *__restrict__ part, int np, const double *__restrict__ g, long long n,
+                           double *__restrict__ x) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < np; ++i) t += part[i];
+        x[n] = -(g[n] + t);
+    }
+}
+
+// partial dot products of the columns i <= j of V with w: block (x, i) sums its row range
+__global__ void __launch_bounds__(256) k_gm_dots(const double *__restrict__ V, const double *__restrict__ w,
+                                                 long long n, const GmresState *__restrict__ s,
+                                                 double *__restrict__ gpart) {
+    __shared__ double ws[8];
+    const int i = blockIdx.y;
+    if (!s->active || i > s->j) return;
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * chunk, hi = min(n, lo + chunk);
+    const double *c = V + (size_t)i * n;
+    double t = 0.0;
+    for (long long r = lo + threadIdx.x; r < hi; r += blockDim.x) t += c[r] * w[r];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) u += ws[k];
+        gpart[(size_t)i * gridDim.x + blockIdx.x] = u;
+    }
+}
+
+// h_i = sum of the partials (fixed order); H(i, j) (+)= h_i; hbuf = h
+__global__ void k_gm_hsum(const double *__restrict__ gpart, int nparts, const GmresState *__restrict__ s,
+                          double *__restrict__ H, double *__restrict__ hbuf, int accumulate) {
+    if (!s->active) return;
+    const int j = s->j, ld = s->m + 1;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double h = 0.0;
+        for (int k = 0; k < nparts; ++k) h += gpart[(size_t)i * nparts + k];
+        hbuf[i] = h;
+        H[i + (size_t)j * ld] = accumulate ? H[i + (size_t)j * ld] + h : h;
+    }
+}
+
+// w -= V(:, 0..j) h
+__global__ void k_gm_sub(const double *__restrict__ V, const double *__restrict__ hbuf,
+                         const GmresState *__restrict__ s, long long n, double *__restrict__ w) {
+    if (!s->active) return;
+    const int j = s->j;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        double t = w[r];
+        for (int i = 0; i <= j; ++i) t -= hbuf[i] * V[(size_t)i * n + r];
+        w[r] = t;
+    }
+}
+
+// H(j + 1, j) = ||w|| (squared norm in `part`)
+__global__ void k_gm_norm(const double *__restrict__ part, int np, GmresState *s, double *__restrict__ H) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || !s->active) return;
+    double t = 0.0;
+    for (int i = 0; i < np; ++i) t += part[i];
+    const double h = sqrt(fmax(t, 0.0));
+    s->hnext = h;
+    H[(s->j + 1) + (size_t)s->j * (s->m + 1)] = h;
+}
+
+// V(:, j + 1) = w / H(j + 1, j) (zero after a lucky breakdown)
+__global__ void k_gm_next(const double *__restrict__ w, const GmresState *__restrict__ s, long long n,
+                          double *__restrict__ V) {
+    if (!s->active) return;
+    const double h = s->hnext, f = h > 0.0 ? 1.0 / h : 0.0;
+    double *c = V + (size_t)(s->j + 1) * n;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        c[r] = f * w[r];
+}
+
+// Givens rotations on column j, the residual norm |g_{j+1}|, the stop test
+__global__ void k_gm_step(GmresState *s, double *H, double *cs, double *sn, double *g,
+                          cudaGraphConditionalHandle loop) {
+    if (s->active) {
+        const int j = s->j, ld = s->m + 1;
+        double *h = H + (size_t)j * ld;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+            h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+            h[i] = t;
+        }
+        const double rho = hypot(h[j], h[j + 1]);
+        if (rho == 0.0) {
+            s->status = 2;
+            s->active = 0;
+        } else {
+            cs[j] = h[j] / rho;
+            sn[j] = h[j + 1] / rho;
+            h[j] = rho;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            s->j = j + 1;
+            s->resid = fabs(g[j + 1]);
+            if (s->resid <= s->rtol * s->beta || s->j >= s->m) s->active = 0;
+        }
+    }
+    if (loop) cudaGraphSetConditional(loop, s->active ? 1u : 0u);
+}
+
+// y = H(:j, :j)^{-1} g(:j) by back substitution
+__global__ void k_gm_solve(const GmresState *__restrict__ s, const double *__restrict__ H,
+                           const double *__restrict__ g, double *__restrict__ yv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = s->j, ld = s->m + 1;
+    for (int i = j - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < j; ++k) t -= H[i + (size_t)k * ld] * yv[k];
+        yv[i] = t / H[i + (size_t)i * ld];
+    }
+}
+
+// u = V(:, :j) y
+__global__ void k_gm_combine(const double *__restrict__ V, const double *__restrict__ yv,
+                             const GmresState *__restrict__ s, long long n, double *__restrict__ u) {
+    const int j = s->j;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int i = 0; i < j; ++i) t += yv[i] * V[(size_t)i * n + r];
+        u[r] = t;
+    }
+}
+
 // ------------------------------------------------------------------ solver state
 struct Solver {
     anova_plan *p32 = nullptr, *p64 = nullptr;
@@ -308,6 +480,14 @@ struct Solver {
     cudaGraphExec_t exec = nullptr;
     const double *graph_b = nullptr;  // buffers the graph was captured with
     double *graph_x = nullptr;
+    // GMRES (svm_opts.krylov = SVM_KRYLOV_GMRES): basis, Hessenberg data and its graph
+    int gm_m = 0;
+    GmresState *gs = nullptr;
+    double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr, *hbuf = nullptr,
+           *gpart = nullptr, *bnorm2 = nullptr;
+    double *vj = nullptr, *z = nullptr, *w = nullptr, *u = nullptr;
+    cudaGraph_t gm_graph = nullptr;
+    cudaGraphExec_t gm_exec = nullptr;
 
     anova_status dot(const double *a, const double *b, long long len, double *out) {
         const int nb = blocks_for(len);
@@ -469,6 +649,101 @@ anova_status minres(Solver &S, const double *b, double *x, double rtol, int maxi
     return ANOVA_OK;
 }
 
+// x = P^{-1} g for the paper's P = [[A^, 0], [-y^T, -1]] (Sec. 5)
+anova_status tri_apply(Solver &S, const double *g, double *x) {
+    anova_status s;
+    if ((s = woodbury_apply(S.lr, S.theta, S.y, g, x, false)) != ANOVA_OK) return s;
+    const int nb = blocks_for(S.n);
+    k_dot<<<nb, 256, 0, S.st>>>(S.y, x, S.n, S.part);
+    k_tri_last<<<1, 32, 0, S.st>>>(S.part, nb, g, S.n, x);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    return ANOVA_OK;
+}
+
+// One GMRES iteration (column j of the Arnoldi process) on stream S.st.
+anova_status gmres_iteration(Solver &S, cudaGraphConditionalHandle loop) {
+    const long long N1 = S.n + 1;
+    const int nb = blocks_for(N1);
+    cudaStream_t st = S.st;
+    anova_status s;
+    k_gm_col<<<nb, 256, 0, st>>>(S.V, S.gs, N1, S.vj);
+    if ((s = tri_apply(S, S.vj, S.z)) != ANOVA_OK) return s;
+    if ((s = S.apply(S.z, S.w, false)) != ANOVA_OK) return s;
+    for (int pass = 0; pass < 2; ++pass) {
+        k_gm_dots<<<dim3(kGsBlocks, S.gm_m + 1), 256, 0, st>>>(S.V, S.w, N1, S.gs, S.gpart);
+        k_gm_hsum<<<1, 128, 0, st>>>(S.gpart, kGsBlocks, S.gs, S.H, S.hbuf, pass);
+        k_gm_sub<<<nb, 256, 0, st>>>(S.V, S.hbuf, S.gs, N1, S.w);
+    }
+    k_dot<<<nb, 256, 0, st>>>(S.w, S.w, N1, S.part);
+    k_gm_norm<<<1, 32, 0, st>>>(S.part, nb, S.gs, S.H);
+    k_gm_next<<<nb, 256, 0, st>>>(S.w, S.gs, N1, S.V);
+    k_gm_step<<<1, 1, 0, st>>>(S.gs, S.H, S.cs, S.sn, S.g, loop);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    return ANOVA_OK;
+}
+
+anova_status build_gmres_graph(Solver &S) {
+    if (!S.cap) ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
+    ANOVA_CUDA_TRY(cudaGraphCreate(&S.gm_graph, 0));
+    cudaGraphConditionalHandle loop = 0;
+    ANOVA_CUDA_TRY(cudaGraphConditionalHandleCreate(&loop, S.gm_graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    ANOVA_CUDA_TRY(cudaGraphAddNode(&node, S.gm_graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t saved[3] = {S.st, S.p32->stream, S.lr->plan->stream};
+    S.st = S.p32->stream = S.lr->plan->stream = S.cap;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(S.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    anova_status s = ANOVA_OK;
+    if (e == cudaSuccess) {
+        s = gmres_iteration(S, loop);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(S.cap, &captured);
+        if (e2 != cudaSuccess && s == ANOVA_OK) s = cuda_fail(e2, "cudaStreamEndCapture");
+    } else {
+        s = cuda_fail(e, "cudaStreamBeginCaptureToGraph");
+    }
+    S.st = saved[0];
+    S.p32->stream = saved[1];
+    S.lr->plan->stream = saved[2];
+    if (s != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaGraphInstantiate(&S.gm_exec, S.gm_graph, 0));
+    return ANOVA_OK;
+}
+
+// Right-preconditioned GMRES for A x = b on the FP32 operator, x0 = 0 (one graph launch for the
+// Arnoldi loop, then the small triangular solve and x = P^{-1} V y).
+anova_status gmres(Solver &S, const double *b, double *x, double rtol, int *iters) {
+    const long long N1 = S.n + 1;
+    const int nb = blocks_for(N1);
+    cudaStream_t st = S.st;
+    anova_status s;
+    if (!S.gm_exec) {
+        if ((s = S.apply(S.z, S.w, false)) != ANOVA_OK) return s;  // the operator must not allocate in the graph
+        if ((s = build_gmres_graph(S)) != ANOVA_OK) return s;
+    }
+    k_dot<<<nb, 256, 0, st>>>(b, b, N1, S.part);
+    k_sum_to<<<1, 32, 0, st>>>(S.part, nb, 1.0, S.bnorm2);
+    k_gm_init<<<1, 1, 0, st>>>(S.gs, S.bnorm2, rtol, S.gm_m, S.g);
+    k_gm_first<<<nb, 256, 0, st>>>(b, S.gs, N1, S.V);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    ANOVA_CUDA_TRY(cudaGraphLaunch(S.gm_exec, st));
+    k_gm_solve<<<1, 1, 0, st>>>(S.gs, S.H, S.g, S.yv);
+    k_gm_combine<<<nb, 256, 0, st>>>(S.V, S.yv, S.gs, N1, S.u);
+    if ((s = tri_apply(S, S.u, x)) != ANOVA_OK) return s;
+    int fin[4];
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(fin, &S.gs->j, sizeof(fin), cudaMemcpyDeviceToHost, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    *iters = fin[0];
+    S.krylov_total += *iters;
+    if (fin[3] == 2) return fail(ANOVA_ERR_BREAKDOWN, "GMRES: singular Hessenberg matrix");
+    return ANOVA_OK;
+}
+
 }  // namespace
 }  // namespace anova
 
@@ -531,6 +806,7 @@ void svm_opts_default(svm_opts *o) {
     o->krylov_tol = 1e-8;
     o->refine_max = 4;
     o->precond = PCHOL_GREEDY;
+    o->krylov = SVM_KRYLOV_MINRES;
     o->rank = 200;
     o->err_tol = 1e-5;
     o->seed = 0;
@@ -557,6 +833,8 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         if (!(C > 0.0) || !std::isfinite(C)) return fail(ANOVA_ERR_INVALID_ARG, "C must be positive");
         if (!(tol > 0.0)) return fail(ANOVA_ERR_INVALID_ARG, "tol must be positive");
         if (o.max_iter < 1 || o.krylov_max < 1 || o.refine_max < 1 || !(o.sigma_barrier > 0 && o.sigma_barrier < 1) ||
+            (o.krylov != SVM_KRYLOV_MINRES && o.krylov != SVM_KRYLOV_GMRES) ||
+            (o.krylov == SVM_KRYLOV_GMRES && o.krylov_max > 1000) ||
             !(o.gamma > 0 && o.gamma < 1) || !(o.krylov_tol > 0) || !(o.ell > 0))
             return fail(ANOVA_ERR_INVALID_ARG, "invalid svm_opts");
         bool has_pos = false, has_neg = false;
@@ -642,12 +920,27 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                   dalloc(sizeof(double) * n, (void **)&S.t64) && dalloc(sizeof(double) * n, (void **)&S.k64);
         for (int k = 0; k < 10 && ok; ++k) ok = dalloc(sizeof(double) * N1, (void **)&work[k]);
         ok = ok && dalloc(sizeof(MinresState), (void **)&S.ms);
+        if (o.krylov == SVM_KRYLOV_GMRES) {
+            const int m = o.krylov_max;
+            S.gm_m = m;
+            ok = ok && dalloc(sizeof(GmresState), (void **)&S.gs) &&
+                 dalloc(sizeof(double) * N1 * (m + 1), (void **)&S.V) &&
+                 dalloc(sizeof(double) * (size_t)(m + 1) * m, (void **)&S.H) && dalloc(sizeof(double) * m, (void **)&S.cs) &&
+                 dalloc(sizeof(double) * m, (void **)&S.sn) && dalloc(sizeof(double) * (m + 1), (void **)&S.g) &&
+                 dalloc(sizeof(double) * m, (void **)&S.yv) && dalloc(sizeof(double) * (m + 1), (void **)&S.hbuf) &&
+                 dalloc(sizeof(double) * kGsBlocks * (m + 1), (void **)&S.gpart) &&
+                 dalloc(sizeof(double), (void **)&S.bnorm2) && dalloc(sizeof(double) * N1, (void **)&S.vj) &&
+                 dalloc(sizeof(double) * N1, (void **)&S.z) && dalloc(sizeof(double) * N1, (void **)&S.w) &&
+                 dalloc(sizeof(double) * N1, (void **)&S.u);
+        }
         if (!ok) return fail(ANOVA_ERR_OOM, "solver allocation failed");
         struct HostRes {
             Solver &s;
             ~HostRes() {
                 if (s.exec) cudaGraphExecDestroy(s.exec);
                 if (s.graph) cudaGraphDestroy(s.graph);
+                if (s.gm_exec) cudaGraphExecDestroy(s.gm_exec);
+                if (s.gm_graph) cudaGraphDestroy(s.gm_graph);
                 if (s.cap) {
                     cudaStreamSynchronize(s.cap);
                     cudaStreamDestroy(s.cap);
@@ -718,7 +1011,11 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             bool solved = false;
             for (int k = 0; k < o.refine_max; ++k) {
                 int iters = 0;
-                if ((s = minres(S, dr, dcorr, inner_tol, o.krylov_max, work, &iters)) != ANOVA_OK) return s;
+                if (o.krylov == SVM_KRYLOV_GMRES) {
+                    if ((s = gmres(S, dr, dcorr, inner_tol, &iters)) != ANOVA_OK) return s;
+                } else if ((s = minres(S, dr, dcorr, inner_tol, o.krylov_max, work, &iters)) != ANOVA_OK) {
+                    return s;
+                }
                 k_axpy<<<blocks_for(N1), 256, 0, st>>>(1.0, dcorr, N1, ddelta);
                 if ((s = S.apply(ddelta, dtmp, true)) != ANOVA_OK) return s;
                 k_sub<<<blocks_for(N1), 256, 0, st>>>(drhs, dtmp, N1, dr);

@@ -80,10 +80,11 @@ def test_large_C_workload3_like(env, C):
     assert abs(d_gpu - d_ref) <= 1e-6 * abs(d_ref)
 
 
-@pytest.mark.parametrize("kind", ["random", "nystrom"])
+@pytest.mark.parametrize("kind", ["random", "nystrom", "gmres"])
 def test_other_preconditioners_reach_the_same_optimum(env, kind):
-    """The optimum does not depend on the preconditioner: randomly pivoted Cholesky and Nystrom
-    reach the dense-KKT oracle's dual objective on workload 1 (only iteration counts differ)."""
+    """The optimum does not depend on the preconditioner or the Krylov method: randomly pivoted
+    Cholesky, Nystrom, and GMRES with the paper's block-triangular preconditioner (Sec. 5) reach
+    the dense-KKT oracle's dual objective on workload 1 (only iteration counts differ)."""
     torch, ab = env
     cfg = config1()
     X, y, W, C = cfg["X"], cfg["y"], cfg["windows"], cfg["C"]
@@ -91,11 +92,29 @@ def test_other_preconditioners_reach_the_same_optimum(env, kind):
     o.rank = 200
     o.krylov_tol = 1e-8
     o.max_iter = 100
-    o.precond = ab.PCHOL_RANDOM if kind == "random" else ab.NYSTROM
+    o.precond = {"random": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM, "gmres": ab.PCHOL_GREEDY}[kind]
+    o.krylov = ab.SVM_KRYLOV_GMRES if kind == "gmres" else ab.SVM_KRYLOV_MINRES
     o.seed = 2023
     alpha, b, st, status = ab.svm_ipm_solve(X, y, C, 1e-6, opts=o, windows=W)
     assert status == ab.ANOVA_OK
     K = ok.anova_kernel_matrix(X, W, cfg["sigma"])
     ref = oi.ipm_dense(K, y, C, tol=1e-9, max_iter=200)
+    d_ref = oi.dual_objective(K, y, ref["alpha"])
+    assert abs(oi.dual_objective(K, y, alpha) - d_ref) <= 1e-6 * abs(d_ref)
+
+
+def test_gmres_large_C(env):
+    """GMRES with the block-triangular preconditioner on the harder C = 100 case."""
+    torch, ab = env
+    cfg = small_problem(400, 6, seed=11)
+    X, y, W = cfg["X"], cfg["y"], cfg["windows"]
+    o = ab.svm_opts_default()
+    o.rank = 100
+    o.max_iter = 150
+    o.krylov = ab.SVM_KRYLOV_GMRES
+    alpha, b, st, status = ab.svm_ipm_solve(X, y, 100.0, 1e-7, opts=o, windows=W)
+    assert status == ab.ANOVA_OK
+    K = ok.anova_kernel_matrix(X, W, 1.0)
+    ref = oi.ipm_dense(K, y, 100.0, tol=1e-10, max_iter=400)
     d_ref = oi.dual_objective(K, y, ref["alpha"])
     assert abs(oi.dual_objective(K, y, alpha) - d_ref) <= 1e-6 * abs(d_ref)
