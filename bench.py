@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study"],
                     help="matvec (default, the headline line) or ipm_batch (independent SVM "
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
@@ -459,6 +459,60 @@ def run_serve(args):
     return 0
 
 
+def run_precond_study(args):
+    """Synthetic analogue of the paper's preconditioner comparison (Sec. 6, the setup-time and
+    Krylov-iteration figures): workload-3-like data (8 Gaussian + 4 binary features, tanh teacher,
+    5 % flips) at several training sizes; for each low-rank factor (greedy and randomly pivoted
+    Cholesky, Nystrom) and rank, the factor's setup time on the FP64 plan and the mean number of
+    GMRES iterations per IPM step (the paper's solver), plus the MINRES count for comparison.
+    sigma = 0.5 and err_tol = 0, so that every factor reaches the rank asked for."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import config3
+    kinds = {"cholesky_greedy": ab.PCHOL_GREEDY, "cholesky_rp": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM}
+    rows = []
+    for n in (5000, 20000, 50000):
+        cfg = config3(n=n)
+        X, y, W = cfg["X"], cfg["y"], cfg["windows"]
+        p64 = ab.anova_nfft_plan(X, W, 0.5, N=64, m=6, flags=ab.ANOVA_FP64)
+        for rank in (50, 100, 200, 400):
+            for name, kind in kinds.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lr = ab.lowrank_precond_build(p64, kind, rank, 0.0, seed=7)
+                torch.cuda.synchronize()
+                setup_ms = 1000 * (time.perf_counter() - t0)
+                got_rank, _ = ab.lowrank_info(lr)
+                lr.destroy()
+                row = {"n_train": n, "rank": rank, "factor": name, "rank_reached": got_rank,
+                       "setup_ms": round(setup_ms, 2)}
+                for krylov, label in ((ab.SVM_KRYLOV_GMRES, "gmres"), (ab.SVM_KRYLOV_MINRES, "minres")):
+                    o = ab.svm_opts_default()
+                    o.rank = rank
+                    o.precond = kind
+                    o.seed = 7
+                    o.err_tol = 0.0
+                    o.ell = 0.5
+                    o.krylov = krylov
+                    o.max_iter = 100
+                    o.krylov_tol = 1e-6
+                    t0 = time.perf_counter()
+                    _, _, st, status = ab.svm_ipm_solve(X, y, 10.0, 1e-6, opts=o, windows=W)
+                    row[label] = {"ipm_iterations": st["iterations"],
+                                  "krylov_per_ipm_step": round(st["krylov_iterations"] / max(1, st["iterations"]), 2),
+                                  "solve_s": round(time.perf_counter() - t0, 3), "converged": st["converged"],
+                                  "rel_gap": st["rel_gap"]}
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+        p64.destroy()
+    print(json.dumps({"metric": "preconditioner study (setup ms, Krylov iterations per IPM step)",
+                      "data": "synthetic (workload 3 generator), C = 10, sigma = 0.5, err_tol 0, gap 1e-6",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -467,6 +521,8 @@ def main():
         return run_ipm_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "precond_study":
+        return run_precond_study(args)
     return run_ours(args)
 
 
