@@ -191,3 +191,16 @@ def rp_cholesky(K, k, seed, err_tol=0.0, pick=None):
         piv.append(s)
     r = len(piv)
     return L[:, :r].copy(), np.array(piv, dtype=np.int64)
+
+
+def per_window_cholesky(Ks, k, err_tol=0.0):
+    """Per-window stacked factors (Sec. 4, the stacking of per-window low-rank factors):
+    sum_l K_l ~ sum_l L_l L_l^T = [L_1 ... L_P][L_1 ... L_P]^T, each L_l the greedy pivoted
+    Cholesky (Algorithm 2) of one window's kernel matrix K_l at rank k. Returns the stacked factor
+    (n x sum of the ranks reached) and the pivots, window after window."""
+    Ls, pivs = [], []
+    for K in Ks:
+        L, piv = pivoted_cholesky(K, k, err_tol)
+        Ls.append(L)
+        pivs.append(piv)
+    return np.hstack(Ls), np.concatenate(pivs)

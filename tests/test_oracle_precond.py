@@ -194,3 +194,18 @@ def test_rp_cholesky_with_argmax_draws_is_algorithm_2():
     L, piv = op.rp_cholesky(K, 12, seed=0, pick=lambda d, j: int(np.argmax(d)))
     assert piv.tolist() == pg.tolist()
     assert np.allclose(L, Lg, atol=1e-12)
+
+
+def test_per_window_stacked_factor():
+    """Stacking per-window factors: at full rank per window the product is the summed kernel, and
+    each block of columns is Algorithm 2 on its own window's matrix."""
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-0.2, 0.2, size=(30, 6))
+    W = np.array([[0, 1, 2], [3, 4, 5]])
+    Ks = [ok.window_kernel_matrix(X, w, 0.3) for w in W]
+    L, piv = op.per_window_cholesky(Ks, 30)
+    assert np.allclose(L @ L.T, ok.anova_kernel_matrix(X, W, 0.3), atol=1e-9)
+    L1, p1 = op.pivoted_cholesky(Ks[0], 30)
+    assert np.array_equal(piv[: p1.size], p1) and np.allclose(L[:, : p1.size], L1)
+    Lk, _ = op.per_window_cholesky(Ks, 5)
+    assert Lk.shape == (30, 10)
