@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=1.0,
                     help="serve: mean arrival rate of requests (Poisson, requests/s)")
     ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: device-memory budget")
+    ap.add_argument("--factors", default="cholesky_greedy,cholesky_rp,nystrom,cholesky_per_window",
+                    help="precond_study: comma-separated low-rank factors to compare")
+    ap.add_argument("--sizes", default="5000,20000,50000", help="precond_study: training sizes")
     return ap.parse_args()
 
 
@@ -463,7 +466,7 @@ def run_precond_study(args):
     """Synthetic analogue of the paper's preconditioner comparison (Sec. 6, the setup-time and
     Krylov-iteration figures): workload-3-like data (8 Gaussian + 4 binary features, tanh teacher,
     5 % flips) at several training sizes; for each low-rank factor (greedy and randomly pivoted
-    Cholesky, Nystrom) and rank, the factor's setup time on the FP64 plan and the mean number of
+    Cholesky, Nystrom, per-window stacked greedy factors) and rank, the factor's setup time on the FP64 plan and the mean number of
     GMRES iterations per IPM step (the paper's solver), plus the MINRES count for comparison.
     sigma = 0.5 and err_tol = 0, so that every factor reaches the rank asked for."""
     import torch
@@ -471,9 +474,11 @@ def run_precond_study(args):
     __graft_entry__.build()
     import paper_2312_00538_gb300 as ab
     from synth import config3
-    kinds = {"cholesky_greedy": ab.PCHOL_GREEDY, "cholesky_rp": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM}
+    all_kinds = {"cholesky_greedy": ab.PCHOL_GREEDY, "cholesky_rp": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM,
+                 "cholesky_per_window": ab.PCHOL_PER_WINDOW}
+    kinds = {k: all_kinds[k] for k in args.factors.split(",")}
     rows = []
-    for n in (5000, 20000, 50000):
+    for n in (int(v) for v in args.sizes.split(",")):
         cfg = config3(n=n)
         X, y, W = cfg["X"], cfg["y"], cfg["windows"]
         p64 = ab.anova_nfft_plan(X, W, 0.5, N=64, m=6, flags=ab.ANOVA_FP64)

@@ -38,6 +38,11 @@ extern "C" {
  *          point order) with cumsum(max(d, 0))[s] > u_j sum(max(d, 0)), where u_j is output j of
  *          SplitMix64 started at `seed` (state seed + (j + 1) 0x9E3779B97F4A7C15 through its
  *          finaliser), top 53 bits scaled to [0, 1). Columns and stop rule as PCHOL_GREEDY.
+ *   kind = PCHOL_PER_WINDOW: per-window stacked factors (Sec. 4): K_l ~ L_l L_l^T by Algorithm 2
+ *          on window l's kernel alone, at rank r / P (at least 1) each, stop rule relative to
+ *          eta_l; L = [L_1 ... L_P] in the plan's internal window order (windows sorted by
+ *          decreasing dimension, stable), rank = the sum of the ranks reached; pivots are listed
+ *          window after window, each window's from index 0.
  * seed is used by PCHOL_RANDOM only.
  * The plan must outlive the preconditioner. Requires eta_l >= 0 (K positive semidefinite).
  * Errors: INVALID_ARG (r outside [1, 1024], bad kind, negative eta), OOM, CUDA.
@@ -103,7 +108,7 @@ typedef struct {
     int refine_max;          /* FP64 refinement passes per Newton solve (default 4); when the
                                 FP32-operator passes stop reducing the FP64 residual, the solve
                                 finishes with MINRES on the FP64 operator */
-    int precond;             /* PCHOL_GREEDY, NYSTROM or PCHOL_RANDOM (with `seed`) */
+    int precond;             /* PCHOL_GREEDY, NYSTROM, PCHOL_RANDOM (with `seed`) or PCHOL_PER_WINDOW */
     int rank;                /* preconditioner rank (default 200, at most n) */
     double err_tol;          /* pivoted-Cholesky tolerance (Table 1: 1e-5) */
     uint64_t seed;

@@ -33,6 +33,7 @@ ANOVA_INTERP_SIMT = 4
 PCHOL_GREEDY = 0
 NYSTROM = 1
 PCHOL_RANDOM = 2
+PCHOL_PER_WINDOW = 3
 SVM_KRYLOV_MINRES = 0
 SVM_KRYLOV_GMRES = 1
 

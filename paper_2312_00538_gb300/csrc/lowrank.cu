@@ -512,11 +512,14 @@ void lowrank_release(lowrank *lr) {
     delete lr;
 }
 
+static anova_status lowrank_finish(lowrank *lr);
+static anova_status per_window_build(anova_plan *p, lowrank *lr, int r, double err_tol, int nb);
+
 anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, uint64_t seed, lowrank **out) {
     if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
-    if (kind != PCHOL_GREEDY && kind != NYSTROM && kind != PCHOL_RANDOM)
+    if (kind != PCHOL_GREEDY && kind != NYSTROM && kind != PCHOL_RANDOM && kind != PCHOL_PER_WINDOW)
         return fail(ANOVA_ERR_INVALID_ARG, "unknown preconditioner kind");
     if (r < 1 || r > 1024) return fail(ANOVA_ERR_INVALID_ARG, "rank must be in [1, 1024]");
     if (!(err_tol >= 0.0) || !std::isfinite(err_tol)) return fail(ANOVA_ERR_INVALID_ARG, "err_tol must be >= 0");
@@ -544,6 +547,12 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
         (e = cudaMalloc(&lr->stop, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&lr->partial, 16 * (size_t)nb)) != cudaSuccess)
         return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    if (kind == PCHOL_PER_WINDOW) {
+        anova_status s = per_window_build(p, lr, r, err_tol, nb);
+        if (s != ANOVA_OK) return bail(s);
+        *out = lr;
+        return ANOVA_OK;
+    }
     const KernParams kp = kern_params(p);
     double diag = 0.0;
     for (int w = 0; w < p->P; ++w) diag += p->win[w].eta;   // K_ii = sum_l eta_l
@@ -611,8 +620,22 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
         if (e != cudaSuccess) return bail(cuda_fail(e, "Nystrom kernels"));
         if (e2 != cudaSuccess) return bail(cuda_fail(e2, "Nystrom sync"));
     }
-    if ((e = cudaMalloc(&lr->L32, sizeof(float) * n * rank)) != cudaSuccess)
-        return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    {
+        anova_status s = lowrank_finish(lr);
+        if (s != ANOVA_OK) return bail(s);
+    }
+    *out = lr;
+    return ANOVA_OK;
+}
+
+// FP32 copy of the factor and the Woodbury workspace for rank lr->rank (factor in lr->L64).
+static anova_status lowrank_finish(lowrank *lr) {
+    anova_plan *p = lr->plan;
+    cudaStream_t st = p->stream;
+    const long long n = lr->n;
+    const int rank = lr->rank;
+    if ((cudaMalloc(&lr->L32, sizeof(float) * n * rank)) != cudaSuccess)
+        return fail(ANOVA_ERR_OOM, "low-rank allocation failed");
     k_to_float<<<grid_for(n * rank, 256), 256, 0, st>>>(lr->L64, lr->L32, n * rank);
     // Woodbury workspace
     const int nt = (rank + 31) / 32;
@@ -622,22 +645,74 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
     lr->ntiles = (int)tiles.size();
     lr->nchunks = (int)((n + kCoreRows - 1) / kCoreRows);
     lr->napply = (int)((n + kApplyRows - 1) / kApplyRows);
-    if ((e = cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
-        (e = cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
-        (e = cudaMalloc(&lr->z, sizeof(double) * rank)) != cudaSuccess ||
+    if ((cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->z, sizeof(double) * rank)) != cudaSuccess ||
 
-        (e = cudaMalloc(&lr->upart, sizeof(double) * rank * lr->napply)) != cudaSuccess ||
-        (e = cudaMalloc(&lr->tiles, sizeof(int2) * tiles.size())) != cudaSuccess ||
-        (e = cudaMalloc(&lr->cpart, sizeof(double) * 1024 * tiles.size() * lr->nchunks)) != cudaSuccess ||
-        (e = cudaMalloc(&lr->info, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&lr->tmp, sizeof(double) * (n + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&lr->dpart, sizeof(double) * 1024)) != cudaSuccess ||
-        (e = cudaMalloc(&lr->schur, sizeof(double))) != cudaSuccess)
-        return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+        (cudaMalloc(&lr->upart, sizeof(double) * rank * lr->napply)) != cudaSuccess ||
+        (cudaMalloc(&lr->tiles, sizeof(int2) * tiles.size())) != cudaSuccess ||
+        (cudaMalloc(&lr->cpart, sizeof(double) * 1024 * tiles.size() * lr->nchunks)) != cudaSuccess ||
+        (cudaMalloc(&lr->info, sizeof(int))) != cudaSuccess ||
+        (cudaMalloc(&lr->tmp, sizeof(double) * (n + 1))) != cudaSuccess ||
+        (cudaMalloc(&lr->dpart, sizeof(double) * 1024)) != cudaSuccess ||
+        (cudaMalloc(&lr->schur, sizeof(double))) != cudaSuccess)
+        return fail(ANOVA_ERR_OOM, "low-rank allocation failed");
     ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    *out = lr;
     return ANOVA_OK;
+}
+
+// Per-window stacked factors (Sec. 4): sum_l K_l ~ [L_1 ... L_P][L_1 ... L_P]^T with L_l the
+// greedy pivoted Cholesky (Algorithm 2) of window l's kernel alone, at rank r / P each (at least
+// 1), stacked in the plan's window order; a window that stops early leaves no gap. The stop rule
+// of window l is relative to its own diagonal eta_l.
+static anova_status per_window_build(anova_plan *p, lowrank *lr, int r, double err_tol, int nb) {
+    cudaStream_t st = p->stream;
+    const long long n = lr->n;
+    const int kw = std::max(1, r / p->P);
+    const long long zero = 0;
+    const int minus1 = -1;
+    int col0 = 0;
+    std::vector<long long> piv;
+    for (int l = 0; l < p->P; ++l) {
+        const double eta = p->win[l].eta;
+        const int rl = std::min(kw, r - col0);
+        if (!(eta > 0.0) || rl < 1) continue;
+        KernParams kp;
+        std::memset(&kp, 0, sizeof(kp));
+        kp.P = 1;
+        kp.dw[0] = p->win[l].dw;
+        kp.inv_ell2[0] = 1.0 / (p->win[l].ell * p->win[l].ell);
+        kp.eta[0] = eta;
+        const double *xw = p->xw + (long long)l * 3 * n;
+        double *L = lr->L64 + (long long)col0 * n;
+        long long *pv = (long long *)lr->piv_dev + col0;
+        double *dp = lr->dpiv + col0;
+        k_fill<<<nb, 256, 0, st>>>(lr->d, n, eta);
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(pv, &zero, sizeof(long long), cudaMemcpyHostToDevice, st));
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(dp, &eta, sizeof(double), cudaMemcpyHostToDevice, st));
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->stop, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int j = 0; j < rl; ++j) {
+            k_pchol_column<<<nb, 256, sizeof(double) * std::max(1, j), st>>>(j, xw, n, kp, L, lr->d, pv, dp,
+                                                                           lr->stop, (ValIdx *)lr->partial);
+            k_pchol_pick<<<1, 32, 0, st>>>(j, nb, (const ValIdx *)lr->partial, pv, dp, lr->stop, rl,
+                                           err_tol * eta);
+        }
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        int rank = 0;
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(&rank, lr->stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        if (rank < 1 || rank > rl) return fail(ANOVA_ERR_CUDA, "pivoted Cholesky returned no rank");
+        std::vector<long long> pl(rank);
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(pl.data(), pv, sizeof(long long) * rank, cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        piv.insert(piv.end(), pl.begin(), pl.end());
+        col0 += rank;
+    }
+    if (col0 < 1) return fail(ANOVA_ERR_INVALID_ARG, "kernel diagonal is not positive");
+    lr->rank = col0;
+    lr->piv = piv;
+    return lowrank_finish(lr);
 }
 
 // Woodbury apply of the (n x n) block: x[0:n] = A^{-1} g[0:n]; if with_schur, x[n] = g[n]/s.

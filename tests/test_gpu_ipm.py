@@ -80,11 +80,12 @@ def test_large_C_workload3_like(env, C):
     assert abs(d_gpu - d_ref) <= 1e-6 * abs(d_ref)
 
 
-@pytest.mark.parametrize("kind", ["random", "nystrom", "gmres"])
+@pytest.mark.parametrize("kind", ["random", "nystrom", "gmres", "per_window"])
 def test_other_preconditioners_reach_the_same_optimum(env, kind):
     """The optimum does not depend on the preconditioner or the Krylov method: randomly pivoted
-    Cholesky, Nystrom, and GMRES with the paper's block-triangular preconditioner (Sec. 5) reach
-    the dense-KKT oracle's dual objective on workload 1 (only iteration counts differ)."""
+    Cholesky, Nystrom, per-window stacked factors, and GMRES with the paper's block-triangular
+    preconditioner (Sec. 5) reach the dense-KKT oracle's dual objective on workload 1 (only
+    iteration counts differ)."""
     torch, ab = env
     cfg = config1()
     X, y, W, C = cfg["X"], cfg["y"], cfg["windows"], cfg["C"]
@@ -92,7 +93,8 @@ def test_other_preconditioners_reach_the_same_optimum(env, kind):
     o.rank = 200
     o.krylov_tol = 1e-8
     o.max_iter = 100
-    o.precond = {"random": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM, "gmres": ab.PCHOL_GREEDY}[kind]
+    o.precond = {"random": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM, "gmres": ab.PCHOL_GREEDY,
+                 "per_window": ab.PCHOL_PER_WINDOW}[kind]
     o.krylov = ab.SVM_KRYLOV_GMRES if kind == "gmres" else ab.SVM_KRYLOV_MINRES
     o.seed = 2023
     alpha, b, st, status = ab.svm_ipm_solve(X, y, C, 1e-6, opts=o, windows=W)

@@ -122,3 +122,44 @@ def test_randomly_pivoted_cholesky_err_tol_stop(env):
     Lo, pivo = op.rp_cholesky(K, 200, seed=99, err_tol=1e-5)
     assert np.array_equal(piv, pivo)
     assert np.max(np.diag(K - L @ L.T)) <= 1e-5 * np.max(np.diag(K)) + 1e-13
+
+
+def test_per_window_stacked_factors_match_oracle(env):
+    """Per-window stacked factors: each window's block equals Algorithm 2 on that window's kernel,
+    blocks in the plan's window order (stable, decreasing dimension)."""
+    torch, ab = env
+    rng = np.random.default_rng(17)
+    n = 300
+    X = minmax_scale(rng.standard_normal((n, 6)))
+    W = np.array([[0, -1, -1], [1, 2, 3], [4, 5, -1]], dtype=np.int32)
+    # ell and rank keep every pivot choice clear of rounding (the 1-D window's residual is still
+    # ~1e-5 at its last pivot, with the runner-up ~1e-9 below it)
+    plan = ab.anova_nfft_plan(X, W, 0.2, N=64, m=6, flags=ab.ANOVA_FP64)
+    internal = sorted(range(3), key=lambda l: -int(np.sum(W[l] >= 0)))
+    Ks = [ok.window_kernel_matrix(X, W[l], 0.2) for l in internal]
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_PER_WINDOW, 24, 0.0)
+    L, piv = _factor(torch, ab, lr, n)
+    Lo, pivo = op.per_window_cholesky(Ks, 8)
+    assert L.shape == Lo.shape
+    assert np.array_equal(piv, pivo)
+    assert np.allclose(L, Lo, rtol=0, atol=1e-10)
+
+
+def test_per_window_full_rank_and_early_stop(env):
+    """A one-feature window on binary data has rank 2: its block stops there and the next window's
+    block starts right after it; with enough rank per window L L^T is the summed kernel."""
+    torch, ab = env
+    rng = np.random.default_rng(5)
+    n = 120
+    X = minmax_scale(np.column_stack([rng.integers(0, 2, n), rng.standard_normal((n, 2))]).astype(float))
+    W = np.array([[0, -1, -1], [1, 2, -1]], dtype=np.int32)
+    plan = ab.anova_nfft_plan(X, W, 0.3, N=64, m=6, flags=ab.ANOVA_FP64)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_PER_WINDOW, 240, 1e-12)
+    L, piv = _factor(torch, ab, lr, n)
+    K = ok.anova_kernel_matrix(X, W, 0.3)
+    K1, K0 = (ok.window_kernel_matrix(X, W[l], 0.3) for l in (1, 0))   # plan order: 2-D window first
+    assert L.shape[1] < 240
+    assert np.allclose(L[:, -2:] @ L[:, -2:].T, K0, atol=1e-12)
+    assert np.allclose(L[:, :-2] @ L[:, :-2].T, K1, atol=1e-9)
+    assert np.allclose(L @ L.T, K, atol=1e-9)
+    assert piv[-2] == 0 and X[piv[-1], 0] != X[0, 0]
