@@ -85,9 +85,9 @@ def nystrom_columns(K, idx, rel_threshold=1e-10):
 
 
 def nystrom_random(K, k, seed, rel_threshold=1e-10):
-    """Q = orth(K G) with Gaussian G (n x k), orthonormalised by a Householder QR."""
-    rng = np.random.default_rng(seed)
-    G = rng.standard_normal((K.shape[0], k))
+    """Q = orth(K G) with the Gaussian G = gaussian_matrix(n, k, seed) (Sec. 4, the randomised
+    Nystrom range), orthonormalised by a Householder QR (reading C-16)."""
+    G = gaussian_matrix(K.shape[0], k, seed)
     Q, _ = np.linalg.qr(K @ G)
     return nystrom(K, Q, rel_threshold)
 
@@ -204,3 +204,25 @@ def per_window_cholesky(Ks, k, err_tol=0.0):
         Ls.append(L)
         pivs.append(piv)
     return np.hstack(Ls), np.concatenate(pivs)
+
+
+def splitmix64_array(seed, j):
+    """splitmix64(seed, j) for an integer array j, in wrapping uint64 arithmetic."""
+    j = np.asarray(j, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(int(seed) & _MASK64) + (j + np.uint64(1)) * np.uint64(_GOLDEN_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def gaussian_matrix(n, k, seed):
+    """Standard normal G (n x k) for the randomised Nystrom range K G (Sec. 4), drawn so that any
+    implementation of the same published generators reproduces it: entry (i, j), t = j n + i, is
+    the Box-Muller transform (Box and Muller, 1958) sqrt(-2 ln(1 - u)) cos(2 pi u') of the uniforms
+    u = uniform01(seed, 2t), u' = uniform01(seed, 2t + 1) (1 - u lies in (0, 1], so the log is
+    finite)."""
+    t = np.arange(n * k, dtype=np.uint64).reshape(k, n).T          # column-major t = j n + i
+    u = (splitmix64_array(seed, 2 * t) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    u2 = (splitmix64_array(seed, 2 * t + 1) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(1.0 - u)) * np.cos(2.0 * np.pi * u2)

@@ -209,3 +209,37 @@ def test_per_window_stacked_factor():
     assert np.array_equal(piv[: p1.size], p1) and np.allclose(L[:, : p1.size], L1)
     Lk, _ = op.per_window_cholesky(Ks, 5)
     assert Lk.shape == (30, 10)
+
+
+def test_splitmix64_array_matches_scalar():
+    j = np.array([0, 1, 2, 7, 12345, 2 ** 40 + 3], dtype=np.uint64)
+    for seed in (0, 99, 2 ** 63 + 7):
+        got = op.splitmix64_array(seed, j)
+        assert [int(g) for g in got] == [op.splitmix64(seed, int(x)) for x in j]
+
+
+def test_gaussian_matrix_is_standard_normal():
+    """Box-Muller over SplitMix64: moments and the Kolmogorov-Smirnov distance to N(0, 1)."""
+    from scipy import stats
+    G = op.gaussian_matrix(4000, 5, seed=31)
+    assert G.shape == (4000, 5)
+    g = G.ravel()
+    assert abs(g.mean()) < 0.03 and abs(g.var() - 1.0) < 0.04
+    assert stats.kstest(g, "norm").pvalue > 1e-3
+    # column-major numbering: column j continues where column j - 1 stopped
+    G2 = op.gaussian_matrix(8000, 1, seed=31)
+    assert np.array_equal(G2[4000:, 0], G[:, 1])
+
+
+def test_nystrom_random_depends_on_the_range_only():
+    """(K Q)(Q^T K Q)^{-1}(K Q)^T is the same for every orthonormal basis of range(K G); it is a
+    lower approximation (K - Z Z^T is PSD); it is exact when k reaches the numerical rank."""
+    K, _ = _K(60, 3, 0.5, 13)
+    Zt = op.nystrom_random(K, 8, seed=5)
+    G = op.gaussian_matrix(60, 8, seed=5)
+    R = np.linalg.qr(np.random.default_rng(1).standard_normal((8, 8)))[0]
+    Q2 = np.linalg.svd(K @ G @ R, full_matrices=False)[0]
+    Z2 = op.nystrom(K, Q2)
+    assert np.allclose(Zt @ Zt.T, Z2 @ Z2.T, atol=1e-9)
+    assert np.min(np.linalg.eigvalsh(K - Zt @ Zt.T)) > -1e-9
+    assert np.trace(K - Zt @ Zt.T) < np.trace(K)
