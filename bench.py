@@ -475,7 +475,7 @@ def run_precond_study(args):
     import paper_2312_00538_gb300 as ab
     from synth import config3
     all_kinds = {"cholesky_greedy": ab.PCHOL_GREEDY, "cholesky_rp": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM,
-                 "cholesky_per_window": ab.PCHOL_PER_WINDOW}
+                 "cholesky_per_window": ab.PCHOL_PER_WINDOW, "nystrom_random": ab.NYSTROM_RANDOM}
     kinds = {k: all_kinds[k] for k in args.factors.split(",")}
     rows = []
     for n in (int(v) for v in args.sizes.split(",")):

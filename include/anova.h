@@ -69,7 +69,8 @@ enum {
     PCHOL_GREEDY = 0, /* Algorithm 2: greedy pivoted Cholesky (Sec. 4) */
     NYSTROM = 1,      /* Nystrom K ~ (KQ)(Q^T K Q)^{-1}(KQ)^T with Q = pivoted columns (Sec. 4) */
     PCHOL_RANDOM = 2, /* randomly pivoted Cholesky: pivots drawn by the residual diagonal (Sec. 4) */
-    PCHOL_PER_WINDOW = 3 /* greedy factors of each K_l, stacked: [L_1 ... L_P] (Sec. 4) */
+    PCHOL_PER_WINDOW = 3, /* greedy factors of each K_l, stacked: [L_1 ... L_P] (Sec. 4) */
+    NYSTROM_RANDOM = 4    /* Nystrom with Q = orth(K G), G Gaussian, by matvecs (Sec. 4) */
 };
 
 /*

@@ -43,7 +43,14 @@ extern "C" {
  *          eta_l; L = [L_1 ... L_P] in the plan's internal window order (windows sorted by
  *          decreasing dimension, stable), rank = the sum of the ranks reached; pivots are listed
  *          window after window, each window's from index 0.
- * seed is used by PCHOL_RANDOM only.
+ *   kind = NYSTROM_RANDOM: Nystrom with Q = orth(K G) (Sec. 4), G (n x r, column-major) of
+ *          standard normals, entry t = j n + i the Box-Muller transform sqrt(-2 ln(1 - u))
+ *          cos(2 pi u') of SplitMix64 outputs 2t and 2t + 1 (as above) started at `seed`. K G and
+ *          K Q are multi-RHS matvecs of the plan, which must be FP64 (else INVALID_ARG). Q by
+ *          Gram-Schmidt with re-orthogonalisation; columns whose norm falls below 1e-10 of their
+ *          norm before are dropped, so rank <= r. Core as NYSTROM. err_tol is not used; the
+ *          pivots reported by lowrank_info are -1.
+ * seed is used by PCHOL_RANDOM and NYSTROM_RANDOM only.
  * The plan must outlive the preconditioner. Requires eta_l >= 0 (K positive semidefinite).
  * Errors: INVALID_ARG (r outside [1, 1024], bad kind, negative eta), OOM, CUDA.
  */
@@ -108,7 +115,7 @@ typedef struct {
     int refine_max;          /* FP64 refinement passes per Newton solve (default 4); when the
                                 FP32-operator passes stop reducing the FP64 residual, the solve
                                 finishes with MINRES on the FP64 operator */
-    int precond;             /* PCHOL_GREEDY, NYSTROM, PCHOL_RANDOM (with `seed`) or PCHOL_PER_WINDOW */
+    int precond;             /* PCHOL_GREEDY, NYSTROM, PCHOL_RANDOM, PCHOL_PER_WINDOW, NYSTROM_RANDOM */
     int rank;                /* preconditioner rank (default 200, at most n) */
     double err_tol;          /* pivoted-Cholesky tolerance (Table 1: 1e-5) */
     uint64_t seed;

@@ -34,6 +34,7 @@ PCHOL_GREEDY = 0
 NYSTROM = 1
 PCHOL_RANDOM = 2
 PCHOL_PER_WINDOW = 3
+NYSTROM_RANDOM = 4
 SVM_KRYLOV_MINRES = 0
 SVM_KRYLOV_GMRES = 1
 

@@ -470,17 +470,123 @@ __global__ void __launch_bounds__(1024) k_ldl(double *C, int r, double rel_thres
     }
 }
 
-// Z(:, q) for the Nystrom factor: row i solves L_C z^T = K(S, i) forward, then scales by D^{-1/2}.
+// Z(:, q) for the Nystrom factor: row i solves L_C z^T = (K Q)(i, :) forward, then scales by
+// D^{-1/2}. (K Q)(i, a) is K(i, S_a) for a pivot set S (Wq == nullptr), else Wq[a n + i].
 __global__ void __launch_bounds__(128) k_nystrom_rows(const double *__restrict__ xw, long long n, KernParams kp,
                                                       const long long *__restrict__ piv, const double *__restrict__ C,
-                                                      int r, double *__restrict__ Z) {
+                                                      int r, double *__restrict__ Z, const double *__restrict__ Wq) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         for (int a = 0; a < r; ++a) {
-            double s = kernel_entry(xw, n, i, piv[a], kp);
+            double s = Wq ? Wq[(long long)a * n + i] : kernel_entry(xw, n, i, piv[a], kp);
             for (int b = 0; b < a; ++b) s -= C[(long long)a * r + b] * Z[(long long)b * n + i];
             Z[(long long)a * n + i] = s;
         }
         for (int a = 0; a < r; ++a) Z[(long long)a * n + i] /= sqrt(C[(long long)a * r + a]);
+    }
+}
+
+// ---------------------------------------------------------------- randomised Nystrom (Sec. 4)
+// Entry t = j n + i of the Gaussian G in K G: the Box-Muller transform (Box and Muller, 1958)
+// sqrt(-2 ln(1 - u)) cos(2 pi u') of the SplitMix64 uniforms u = number 2t, u' = number 2t + 1.
+__global__ void k_gauss(double *__restrict__ G, long long cnt, unsigned long long seed) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
+        const double u = splitmix_uniform(seed, 2 * t), u2 = splitmix_uniform(seed, 2 * t + 1);
+        G[t] = sqrt(-2.0 * log(1.0 - u)) * cos(2.0 * 3.141592653589793 * u2);
+    }
+}
+
+constexpr int kOrthRows = 2048;
+
+// part[c * t + q] = sum over row chunk c of Q(i, q) v(i), q < t (one warp per column).
+__global__ void __launch_bounds__(256) k_qt_partial(const double *__restrict__ Q, long long n, int t,
+                                                    const double *__restrict__ v, double *__restrict__ part) {
+    const long long i0 = (long long)blockIdx.x * kOrthRows;
+    const long long i1 = min(n, i0 + kOrthRows);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = blockIdx.y * 8 + warp; q < t; q += gridDim.y * 8) {
+        double s = 0.0;
+        for (long long i = i0 + lane; i < i1; i += 32) s = fma(Q[(long long)q * n + i], v[i], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) part[(long long)blockIdx.x * t + q] = s;
+    }
+}
+
+// h[q] = sum over chunks (fixed order) of part[c * t + q]
+__global__ void k_sum_chunks(const double *__restrict__ part, int nch, int t, double *__restrict__ h) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < t; q += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nch; ++c) s += part[(long long)c * t + q];
+        h[q] = s;
+    }
+}
+
+// v -= Q(:, :t) h
+__global__ void __launch_bounds__(256) k_sub_qh(const double *__restrict__ Q, long long n, int t,
+                                                const double *__restrict__ h, double *__restrict__ v) {
+    extern __shared__ double hs[];
+    for (int q = threadIdx.x; q < t; q += blockDim.x) hs[q] = h[q];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < t; ++q) s = fma(Q[(long long)q * n + i], hs[q], s);
+        v[i] -= s;
+    }
+}
+
+__global__ void k_scale_to(const double *__restrict__ src, long long n, const double *__restrict__ nrm2,
+                           double *__restrict__ dst) {
+    const double inv = 1.0 / sqrt(*nrm2);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i] * inv;
+}
+
+// Partial products S = A^T B of two n x k column-major FP64 panels over row chunks, 32 x 32 tiles
+// (tile index a_tile * nt + b_tile), FP64 accumulation.
+__global__ void __launch_bounds__(256) k_atb_partial(const double *__restrict__ A, const double *__restrict__ B,
+                                                     long long n, int k, int nt, double *__restrict__ part) {
+    __shared__ double As[32][33];
+    __shared__ double Bs[32][33];
+    const int a0 = (blockIdx.x / nt) * 32, b0 = (blockIdx.x % nt) * 32;
+    const long long i0 = (long long)blockIdx.y * kCoreRows;
+    const long long i1 = min(n, i0 + kCoreRows);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double acc[4] = {0, 0, 0, 0};
+    for (long long ib = i0; ib < i1; ib += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int rr = e & 31, cc = e >> 5;
+            const long long i = ib + rr;
+            As[cc][rr] = (i < i1 && a0 + cc < k) ? A[(long long)(a0 + cc) * n + i] : 0.0;
+            Bs[cc][rr] = (i < i1 && b0 + cc < k) ? B[(long long)(b0 + cc) * n + i] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            const double vb = Bs[tx][rr];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][rr], vb, acc[q]);
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q)
+        part[(((long long)blockIdx.y * gridDim.x + blockIdx.x) * 32 + ty + 8 * q) * 32 + tx] = acc[q];
+}
+
+// C = (S + S^T) / 2, S = sum over chunks (fixed order) of the partial tiles; C row-major k x k.
+__global__ void k_atb_sym(const double *__restrict__ part, int nchunks, int nt, int k, double *__restrict__ C) {
+    const int ntiles = nt * nt;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / k), b = (int)(e % k);
+        if (b > a) continue;
+        double sab = 0.0, sba = 0.0;
+        const int tab = (a / 32) * nt + b / 32, tba = (b / 32) * nt + a / 32;
+        for (int c = 0; c < nchunks; ++c) {
+            sab += part[(((long long)c * ntiles + tab) * 32 + a % 32) * 32 + b % 32];
+            sba += part[(((long long)c * ntiles + tba) * 32 + b % 32) * 32 + a % 32];
+        }
+        const double v = 0.5 * (sab + sba);
+        C[(long long)a * k + b] = v;
+        C[(long long)b * k + a] = v;
     }
 }
 
@@ -514,13 +620,17 @@ void lowrank_release(lowrank *lr) {
 
 static anova_status lowrank_finish(lowrank *lr);
 static anova_status per_window_build(anova_plan *p, lowrank *lr, int r, double err_tol, int nb);
+static anova_status nystrom_random_build(anova_plan *p, lowrank *lr, int k, uint64_t seed);
 
 anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, uint64_t seed, lowrank **out) {
     if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
-    if (kind != PCHOL_GREEDY && kind != NYSTROM && kind != PCHOL_RANDOM && kind != PCHOL_PER_WINDOW)
+    if (kind != PCHOL_GREEDY && kind != NYSTROM && kind != PCHOL_RANDOM && kind != PCHOL_PER_WINDOW &&
+        kind != NYSTROM_RANDOM)
         return fail(ANOVA_ERR_INVALID_ARG, "unknown preconditioner kind");
+    if (kind == NYSTROM_RANDOM && p && p->prec != ANOVA_FP64)
+        return fail(ANOVA_ERR_INVALID_ARG, "the randomised Nystrom factor needs an FP64 plan");
     if (r < 1 || r > 1024) return fail(ANOVA_ERR_INVALID_ARG, "rank must be in [1, 1024]");
     if (!(err_tol >= 0.0) || !std::isfinite(err_tol)) return fail(ANOVA_ERR_INVALID_ARG, "err_tol must be >= 0");
     for (int w = 0; w < p->P; ++w)
@@ -547,6 +657,12 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
         (e = cudaMalloc(&lr->stop, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&lr->partial, 16 * (size_t)nb)) != cudaSuccess)
         return bail(fail(ANOVA_ERR_OOM, "low-rank allocation failed"));
+    if (kind == NYSTROM_RANDOM) {
+        anova_status s = nystrom_random_build(p, lr, r, seed);
+        if (s != ANOVA_OK) return bail(s);
+        *out = lr;
+        return ANOVA_OK;
+    }
     if (kind == PCHOL_PER_WINDOW) {
         anova_status s = per_window_build(p, lr, r, err_tol, nb);
         if (s != ANOVA_OK) return bail(s);
@@ -613,7 +729,7 @@ anova_status lowrank_build_impl(anova_plan *p, int kind, int r, double err_tol, 
                                                                             (const long long *)lr->piv_dev, rank, C);
         k_ldl<<<1, 1024, 0, st>>>(C, rank, 1e-10);
         k_nystrom_rows<<<grid_for(n, 128, 152 * 16), 128, 0, st>>>(p->xw, n, kp, (const long long *)lr->piv_dev,
-                                                                    C, rank, lr->L64);
+                                                                    C, rank, lr->L64, nullptr);
         e = cudaGetLastError();
         cudaError_t e2 = cudaStreamSynchronize(st);
         cudaFree(C);
@@ -660,6 +776,76 @@ static anova_status lowrank_finish(lowrank *lr) {
     ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     return ANOVA_OK;
+}
+
+// Randomised Nystrom (Sec. 4): K ~ (K Q)(Q^T K Q)^{-1}(K Q)^T with Q = orth(K G), G the
+// k_gauss matrix. Both products with K are multi-RHS matvecs of the plan. Q comes from classical
+// Gram-Schmidt with one re-orthogonalisation; a column whose norm falls to 1e-10 of its norm
+// before is dropped (the approximation depends only on range(Q), so dropped near-dependent
+// directions change it by about their share of K). Q^T K Q (symmetrised) is factored L D L^T
+// with D clamped at 1e-10 max D, and Z = (K Q) L^{-T} D^{-1/2}.
+static anova_status nystrom_random_build(anova_plan *p, lowrank *lr, int k, uint64_t seed) {
+    cudaStream_t st = p->stream;
+    const long long n = lr->n;
+    struct Bufs {
+        double *A = nullptr, *B = nullptr, *part = nullptr, *h = nullptr, *nrm = nullptr, *dpart = nullptr,
+               *C = nullptr, *cpart = nullptr;
+        ~Bufs() {
+            for (double *b : {A, B, part, h, nrm, dpart, C, cpart})
+                if (b) cudaFree(b);
+        }
+    } bf;
+    const int nch = (int)((n + kOrthRows - 1) / kOrthRows);
+    const int nbd = grid_for(n, 256, 1024);
+    if (cudaMalloc(&bf.A, sizeof(double) * n * k) != cudaSuccess ||
+        cudaMalloc(&bf.B, sizeof(double) * n * k) != cudaSuccess ||
+        cudaMalloc(&bf.part, sizeof(double) * (size_t)nch * k) != cudaSuccess ||
+        cudaMalloc(&bf.h, sizeof(double) * k) != cudaSuccess || cudaMalloc(&bf.nrm, sizeof(double) * 2) != cudaSuccess ||
+        cudaMalloc(&bf.dpart, sizeof(double) * 1024) != cudaSuccess)
+        return fail(ANOVA_ERR_OOM, "low-rank allocation failed");
+    k_gauss<<<grid_for(n * k, 256), 256, 0, st>>>(bf.A, n * k, (unsigned long long)seed);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    anova_status s = run_matvec_t<double>(p, bf.A, bf.B, k, -1);   // Y = K G
+    if (s != ANOVA_OK) return s;
+    // Q = orth(Y) in place: kept columns move to the front of B
+    int t = 0;
+    for (int c = 0; c < k; ++c) {
+        double *v = bf.B + (long long)c * n;
+        k_dot_partial<<<nbd, 256, 0, st>>>(v, v, n, bf.dpart);
+        k_sum_parts<<<1, 32, 0, st>>>(bf.dpart, nbd, bf.nrm);
+        for (int pass = 0; pass < 2 && t > 0; ++pass) {
+            k_qt_partial<<<dim3(nch, std::min(128, (t + 7) / 8)), 256, 0, st>>>(bf.B, n, t, v, bf.part);
+            k_sum_chunks<<<grid_for(t, 128), 128, 0, st>>>(bf.part, nch, t, bf.h);
+            k_sub_qh<<<grid_for(n, 256, 152 * 8), 256, sizeof(double) * t, st>>>(bf.B, n, t, bf.h, v);
+        }
+        k_dot_partial<<<nbd, 256, 0, st>>>(v, v, n, bf.dpart);
+        k_sum_parts<<<1, 32, 0, st>>>(bf.dpart, nbd, bf.nrm + 1);
+        ANOVA_CUDA_TRY(cudaGetLastError());
+        double nr[2];
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(nr, bf.nrm, sizeof(nr), cudaMemcpyDeviceToHost, st));
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!(nr[1] > 1e-20 * nr[0]) || !(nr[1] > 0.0)) continue;   // norm ratio <= 1e-10: dependent
+        k_scale_to<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(v, n, bf.nrm + 1, bf.B + (long long)t * n);
+        ++t;
+    }
+    if (t < 1) return fail(ANOVA_ERR_BREAKDOWN, "K G has no numerically independent column");
+    s = run_matvec_t<double>(p, bf.B, bf.A, t, -1);   // W = K Q
+    if (s != ANOVA_OK) return s;
+    const int nt = (t + 31) / 32;
+    const int nchunks = (int)((n + kCoreRows - 1) / kCoreRows);
+    if (cudaMalloc(&bf.C, sizeof(double) * t * t) != cudaSuccess ||
+        cudaMalloc(&bf.cpart, sizeof(double) * 1024 * (size_t)nt * nt * nchunks) != cudaSuccess)
+        return fail(ANOVA_ERR_OOM, "low-rank allocation failed");
+    k_atb_partial<<<dim3(nt * nt, nchunks), 256, 0, st>>>(bf.B, bf.A, n, t, nt, bf.cpart);
+    k_atb_sym<<<grid_for((long long)t * t, 256), 256, 0, st>>>(bf.cpart, nchunks, nt, t, bf.C);
+    k_ldl<<<1, 1024, 0, st>>>(bf.C, t, 1e-10);
+    const KernParams kp = kern_params(p);
+    k_nystrom_rows<<<grid_for(n, 128, 152 * 16), 128, 0, st>>>(p->xw, n, kp, nullptr, bf.C, t, lr->L64, bf.A);
+    ANOVA_CUDA_TRY(cudaGetLastError());
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    lr->rank = t;
+    lr->piv.assign(t, -1);
+    return lowrank_finish(lr);
 }
 
 // Per-window stacked factors (Sec. 4): sum_l K_l ~ [L_1 ... L_P][L_1 ... L_P]^T with L_l the

@@ -163,3 +163,32 @@ def test_per_window_full_rank_and_early_stop(env):
     assert np.allclose(L[:, :-2] @ L[:, :-2].T, K1, atol=1e-9)
     assert np.allclose(L @ L.T, K, atol=1e-9)
     assert piv[-2] == 0 and X[piv[-1], 0] != X[0, 0]
+
+
+def test_randomised_nystrom_matches_oracle(env):
+    """Q = orth(K G) with the same Box-Muller/SplitMix64 G on both sides; K G and K Q by the FP64
+    plan. Z Z^T depends only on range(Q), so it is compared with the oracle's (Householder QR)."""
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=400, seed=6)
+    lr = ab.lowrank_precond_build(plan, ab.NYSTROM_RANDOM, 20, 0.0, seed=77)
+    Z, piv = _factor(torch, ab, lr, 400)
+    assert Z.shape == (400, 20) and np.all(piv == -1)
+    Zo = op.nystrom_random(K, 20, seed=77)
+    assert np.allclose(Z @ Z.T, Zo @ Zo.T, rtol=0, atol=1e-7 * np.max(K))
+    # a different seed gives a different (but equally valid) approximation
+    lr2 = ab.lowrank_precond_build(plan, ab.NYSTROM_RANDOM, 20, 0.0, seed=78)
+    Z2, _ = _factor(torch, ab, lr2, 400)
+    assert not np.allclose(Z2 @ Z2.T, Z @ Z.T, rtol=0, atol=1e-7 * np.max(K))
+    assert np.min(np.linalg.eigvalsh(K - Z @ Z.T)) > -1e-6 * np.max(K)
+
+
+def test_randomised_nystrom_full_rank_and_fp32_plan(env):
+    torch, ab = env
+    X, W, plan, K, _ = _setup(ab, n=80, ell=0.05)
+    lr = ab.lowrank_precond_build(plan, ab.NYSTROM_RANDOM, 80, 0.0, seed=3)
+    Z, _ = _factor(torch, ab, lr, 80)
+    assert Z.shape[1] == 80
+    assert np.allclose(Z @ Z.T, K, rtol=0, atol=1e-7 * np.max(K))
+    p32 = ab.anova_nfft_plan(X, W, 0.05, N=32, m=4, flags=ab.ANOVA_FP32)
+    with pytest.raises(ab.AnovaError):
+        ab.lowrank_precond_build(p32, ab.NYSTROM_RANDOM, 10, 0.0, seed=3)
