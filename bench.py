@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=1.0,
                     help="serve: mean arrival rate of requests (Poisson, requests/s)")
     ap.add_argument("--budget-gib", type=float, default=64.0, help="serve: device-memory budget")
+    ap.add_argument("--tune", action="store_true",
+                    help="matvec: build the plan with anova_nfft_plan_tuned (launch-setting search)")
     ap.add_argument("--factors", default="cholesky_greedy,cholesky_rp,nystrom,cholesky_per_window",
                     help="precond_study: comma-separated low-rank factors to compare")
     ap.add_argument("--sizes", default="5000,20000,50000", help="precond_study: training sizes")
@@ -232,7 +234,12 @@ def run_ours(args):
     X, W, vseed = workload(n, seed_offset=rank)    # independent problem per rank (weak scaling)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    plan = ab.anova_nfft_plan(X, W, sigma, N=32, m=4, flags=ab.ANOVA_FP32, stream=stream)
+    tune_report = None
+    if args.tune:
+        plan, tune_report = ab.anova_nfft_plan_tuned(X, W, sigma, N=32, m=4, flags=ab.ANOVA_FP32, nrhs=nrhs,
+                                                     reps=5, stream=stream)
+    else:
+        plan = ab.anova_nfft_plan(X, W, sigma, N=32, m=4, flags=ab.ANOVA_FP32, stream=stream)
     torch.cuda.synchronize()
     plan_ms = 1000 * (time.perf_counter() - t0)
     V = matvec_vectors(n, nrhs, vseed)
@@ -345,7 +352,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(n, sigma, nrhs), "global_batch": world * n,
                        "parallelism": "replicas (one independent problem per GPU)" if world > 1 else "single GPU",
-                       "l2": "flushed between steps (512 MiB write)", "plan_ms": plan_ms},
+                       "l2": "flushed between steps (512 MiB write)", "plan_ms": plan_ms,
+                       "plan": ("tuned: %s" % json.dumps(tune_report)) if tune_report else "default settings"},
             "gpu_launches": int(launches),
             "stage_ms_per_step": {k: v2 / args.steps for k, v2 in stage_ms.items()},
             "roofline": roofline,

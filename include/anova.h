@@ -182,6 +182,38 @@ anova_status anova_spread_grid_noalloc(anova_plan_t plan, int l, const void *v, 
  */
 anova_status anova_cross_matvec(anova_plan_t source, anova_plan_t target, const void *w, void *f);
 
+/*
+ * anova_nfft_plan_tuned -- anova_nfft_plan_ex (same arguments and errors) followed by a search
+ * over launch settings that leave the arithmetic of each point-window product unchanged; the
+ * fastest plan is returned. Settings: the points-per-work-item cap of the spread/interpolation
+ * work items (1024, 2048, 4096; each needs its own plan tables); for FP32 plans with m = 4 and a
+ * 3-D window, the tensor-core or the FP32-pipe interpolation (unless `flags` fixes one); right-hand
+ * sides per pass (16, 8, 4, below nrhs); for FP64 plans with P >= 2, windows on concurrent streams
+ * or not. Each setting is timed over `reps` matvecs with `nrhs` columns (after one warm-up call)
+ * with CUDA events on the plan's stream, inputs resident, caches warm (as in Krylov iterations).
+ * Results of the returned plan equal the default plan's up to the order of floating-point sums.
+ * nrhs in [1, 1024], reps in [1, 1000]; report (may be NULL) receives the choice:
+ *   wi_max, interp (ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT, 0 if not searched), rhs_chunk,
+ *   fork_windows (0/1, 0 if not searched), candidates (settings timed), ms (mean ms per matvec at
+ *   the choice), ms_default (the same with anova_nfft_plan_ex's settings).
+ * Allocates n * nrhs elements twice for the timing inputs and frees them before returning.
+ * Errors: those of anova_nfft_plan_ex; INVALID_ARG (nrhs, reps); TIMEOUT (a kernel wait ran out).
+ */
+typedef struct {
+    int wi_max;
+    int interp;
+    int rhs_chunk;
+    int fork_windows;
+    int candidates;
+    double ms;
+    double ms_default;
+} anova_tune_report;
+
+anova_status anova_nfft_plan_tuned(const double *points, int64_t n, int d, const int32_t *windows,
+                                   int P, const double *ell, const double *eta, int N, int m,
+                                   int flags, void *cuda_stream, int nrhs, int reps,
+                                   anova_tune_report *report, anova_plan_t *out);
+
 /* Plan facts. Any output pointer may be NULL. device_bytes = device memory the plan holds. */
 anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
                              int64_t *device_bytes);

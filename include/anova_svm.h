@@ -127,6 +127,7 @@ typedef struct {
     int scale_features;      /* 1: min-max scale every feature into [-0.2, 0.2] first */
     void *cuda_stream;
     int krylov;              /* SVM_KRYLOV_MINRES (default) or SVM_KRYLOV_GMRES */
+    int autotune;            /* 1: both plans by anova_nfft_plan_tuned (nrhs 1, 3 reps); default 0 */
 } svm_opts;
 
 typedef struct {

@@ -60,6 +60,8 @@ _SIGNATURES = {
                                  _vp, ctypes.POINTER(_vp)]),
     "anova_nfft_plan_ex": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _dp, _dp, _c_int, _c_int,
                                     _c_int, _vp, ctypes.POINTER(_vp)]),
+    "anova_nfft_plan_tuned": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _dp, _dp, _c_int, _c_int,
+                                       _c_int, _vp, _c_int, _c_int, _vp, ctypes.POINTER(_vp)]),
     "anova_matvec": (_c_int, [_vp, _vp, _vp, _c_int]),
     "anova_matvec_host": (_c_int, [_vp, _vp, _vp, _c_int]),
     "anova_window_matvec": (_c_int, [_vp, _c_int, _vp, _vp]),
@@ -204,6 +206,32 @@ def anova_nfft_plan_ex(points, windows, ell, eta=None, N=32, m=4, flags=ANOVA_FP
     return Plan(h, X.shape[0], W.shape[0], flags & 1)
 
 
+class anova_tune_report(ctypes.Structure):
+    _fields_ = [("wi_max", ctypes.c_int), ("interp", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
+                ("fork_windows", ctypes.c_int), ("candidates", ctypes.c_int), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double)]
+
+
+def anova_nfft_plan_tuned(points, windows, ell, eta=None, N=32, m=4, flags=ANOVA_FP32, nrhs=1, reps=5,
+                          stream=None):
+    """anova_nfft_plan_tuned: anova_nfft_plan_ex plus the launch-setting search. Returns
+    (plan, report dict)."""
+    X = _f64(points)
+    W = np.ascontiguousarray(windows, dtype=np.int32).reshape(-1, 3)
+    ell = _f64(np.broadcast_to(ell, (W.shape[0],)))
+    eta_p = None
+    if eta is not None:
+        eta = _f64(np.broadcast_to(eta, (W.shape[0],)))
+        eta_p = _ptr(eta, ctypes.c_double)
+    h = _vp()
+    rep = anova_tune_report()
+    _check(lib().anova_nfft_plan_tuned(_ptr(X, ctypes.c_double), X.shape[0], X.shape[1],
+                                       _ptr(W, ctypes.c_int32), W.shape[0], _ptr(ell, ctypes.c_double),
+                                       eta_p, int(N), int(m), int(flags), _stream_handle(stream), int(nrhs),
+                                       int(reps), ctypes.byref(rep), ctypes.byref(h)))
+    return Plan(h, X.shape[0], W.shape[0], flags & 1), {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
 def anova_matvec(plan, v, Kv, nrhs=1):
     """anova_matvec: v, Kv device tensors holding n x nrhs column-major (i.e. shape (nrhs, n)
     contiguous, or (n,) for one right-hand side)."""
@@ -327,7 +355,7 @@ class svm_opts(ctypes.Structure):
                 ("windows", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int),
                 ("N", ctypes.c_int), ("m", ctypes.c_int), ("N_precise", ctypes.c_int),
                 ("m_precise", ctypes.c_int), ("scale_features", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("krylov", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("krylov", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class svm_stats(ctypes.Structure):

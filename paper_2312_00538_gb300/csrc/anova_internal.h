@@ -121,7 +121,10 @@ struct anova_plan {
     // `stream`); window w uses aux[w % kAuxStreams] and work-counter block w % kAuxStreams
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t fork_evt = nullptr, join_evt[3] = {nullptr, nullptr, nullptr};
-    int interp_flags = 0;         // ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT as created
+    int interp_flags = 0;         // ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT as created or tuned
+    int wi_max = anova::kWiMax;   // points per work item (at most); set at plan creation
+    int rhs_chunk = 16;           // right-hand sides per pass of the multi-RHS matvec (1..16)
+    int fork_windows = 1;         // FP64: run windows of one dimension group on the aux streams
     int64_t static_bytes = 0;
 
     // workspace, grown on demand
@@ -164,4 +167,9 @@ template <typename T>
 anova_status run_interp_grid_t(anova_plan *p, int w, const void *grid, void *f);
 template <typename T>
 anova_status run_cross_matvec_t(anova_plan *src, anova_plan *tgt, const void *w, void *f);
+// create_plan with an explicit work-item cap (kSegMax <= wi_max <= 1 << 16)
+anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                            const double *ell, const double *eta, int N, int m, int flags, void *stream,
+                            int wi_max, anova_plan_t *out);
+void destroy_plan(anova_plan *p);
 }  // namespace anova

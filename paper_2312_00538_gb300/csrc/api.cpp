@@ -29,6 +29,9 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
                          const double *ell, const double *eta, int N, int m, int flags,
                          void *stream, anova_plan_t *out);
 void destroy_plan(anova_plan *p);
+anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *windows, int P, const double *ell,
+                       const double *eta, int N, int m, int flags, void *stream, int nrhs, int reps,
+                       anova_tune_report *report, anova_plan_t *out);
 
 // Runs a plan call on the plan's device, restoring the caller's current device afterwards.
 struct DeviceGuard {
@@ -116,6 +119,15 @@ anova_status anova_nfft_plan_ex(const double *points, int64_t n, int d, const in
                                 int flags, void *cuda_stream, anova_plan_t *out) {
     return guarded([&]() -> anova_status {
         return create_plan(points, n, d, windows, P, ell, eta, N, m, flags, cuda_stream, out);
+    });
+}
+
+anova_status anova_nfft_plan_tuned(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                                   const double *ell, const double *eta, int N, int m, int flags,
+                                   void *cuda_stream, int nrhs, int reps, anova_tune_report *report,
+                                   anova_plan_t *out) {
+    return guarded([&]() -> anova_status {
+        return tune_plan(points, n, d, windows, P, ell, eta, N, m, flags, cuda_stream, nrhs, reps, report, out);
     });
 }
 

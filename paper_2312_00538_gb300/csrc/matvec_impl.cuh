@@ -534,7 +534,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
 
 template <typename T>
 anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_window) {
-    const int chunk = std::min(nrhs, 16);
+    const int chunk = std::min(nrhs, std::max(1, std::min(16, p->rhs_chunk)));
     anova_status st = ensure_workspace(p, chunk);
     if (st != ANOVA_OK) return st;
     T *grids = reinterpret_cast<T *>(p->grids);
@@ -547,7 +547,7 @@ anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_wi
     // (measured: 1.94 -> 1.82 ms at n = 7814, three windows). FP32 stages are single launches over
     // all windows that already fill the GPU, and forking them measured slower. Stage timing needs
     // one stream.
-    const bool fork = sizeof(T) == 8 && p->aux[0] && !p->timing && only_window < 0 && p->P >= 2;
+    const bool fork = sizeof(T) == 8 && p->fork_windows && p->aux[0] && !p->timing && only_window < 0 && p->P >= 2;
     for (int r0 = 0; r0 < nrhs; r0 += chunk) {
         const int nr = std::min(chunk, nrhs - r0);
         const T *vr = v + (size_t)r0 * p->n;

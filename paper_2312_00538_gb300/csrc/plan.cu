@@ -233,8 +233,15 @@ void destroy_plan(anova_plan *p) {
 anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
                          const double *ell, const double *eta, int N, int m, int flags,
                          void *stream, anova_plan_t *out) {
+    return create_plan_wi(points, n, d, windows, P, ell, eta, N, m, flags, stream, kWiMax, out);
+}
+
+anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                            const double *ell, const double *eta, int N, int m, int flags, void *stream,
+                            int wi_max, anova_plan_t *out) {
     // ------------------------------------------------------------------ validation
     if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+    if (wi_max < kSegMax || wi_max > (1 << 16)) return fail(ANOVA_ERR_INVALID_ARG, "work-item cap out of range");
     *out = nullptr;
     if (!points || !windows || !ell) return fail(ANOVA_ERR_INVALID_ARG, "NULL input pointer");
     if (n < 1 || n > (int64_t)1 << 30) return fail(ANOVA_ERR_INVALID_ARG, "n must be in [1, 2^30]");
@@ -294,6 +301,7 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
     p->n_os = 2 * N;
     p->prec = prec;
     p->interp_flags = flags & 6;
+    p->wi_max = wi_max;
     p->B = prec == ANOVA_FP64 ? 2 : 4;
     p->NB = p->n_os / p->B;
     p->tile_w = p->B + 2 * m - 1;
@@ -453,8 +461,8 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
                 }
                 const int packed = c[0] | (c[1] << 10) | (c[2] << 20);
                 segs.push_back(make_int4(packed, (int)q, 0, w));
-                // work items: runs of one bin's segments, at most kWiMax points
-                if ((int)bin != cur_bin || wi_pts + kSegMax > kWiMax) {
+                // work items: runs of one bin's segments, at most wi_max points
+                if ((int)bin != cur_bin || wi_pts + kSegMax > p->wi_max) {
                     int bc[3] = {0, 0, 0};
                     uint32_t b2 = bin;
                     for (int k = dw - 1; k >= 0; --k) { bc[k] = (int)(b2 % NB); b2 /= NB; }
@@ -581,7 +589,7 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
                             return fail(ANOVA_ERR_CUDA, "plan check: segment outside its bin");
                     }
                 }
-                if (pts > kWiMax) return fail(ANOVA_ERR_CUDA, "plan check: work item too large");
+                if (pts > p->wi_max) return fail(ANOVA_ERR_CUDA, "plan check: work item too large");
             }
             int nbins = 1;
             for (int k = 0; k < wi.dw; ++k) nbins *= NB;

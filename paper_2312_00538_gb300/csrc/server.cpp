@@ -77,6 +77,8 @@ int64_t svm_request_footprint(int64_t n, int P, const svm_opts *opts) {
     b += n * 8 * 48;                      // iterates, Krylov vectors and scratch of the solver
     if (o.krylov == SVM_KRYLOV_GMRES) b += (n + 1) * 8 * (int64_t)(o.krylov_max + 5);  // GMRES basis
     b += n * 8 * 3;                       // the points on the device
+    if (o.autotune)                       // a candidate plan and the timing vectors while tuning
+        b += plan_bytes(n, P, o.N_precise, o.m_precise, 2, 8) + n * 8 * 2;
     return b + ((int64_t)16 << 20);       // fixed tables and reduction scratch
 }
 

@@ -23,6 +23,9 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
                          const double *ell, const double *eta, int N, int m, int flags,
                          void *stream, anova_plan_t *out);
 void destroy_plan(anova_plan *p);
+anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *windows, int P, const double *ell,
+                       const double *eta, int N, int m, int flags, void *stream, int nrhs, int reps,
+                       anova_tune_report *report, anova_plan_t *out);
 
 namespace {
 
@@ -807,6 +810,7 @@ void svm_opts_default(svm_opts *o) {
     o->refine_max = 4;
     o->precond = PCHOL_GREEDY;
     o->krylov = SVM_KRYLOV_MINRES;
+    o->autotune = 0;
     o->rank = 200;
     o->err_tol = 1e-5;
     o->seed = 0;
@@ -834,7 +838,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         if (!(tol > 0.0)) return fail(ANOVA_ERR_INVALID_ARG, "tol must be positive");
         if (o.max_iter < 1 || o.krylov_max < 1 || o.refine_max < 1 || !(o.sigma_barrier > 0 && o.sigma_barrier < 1) ||
             (o.krylov != SVM_KRYLOV_MINRES && o.krylov != SVM_KRYLOV_GMRES) ||
-            (o.krylov == SVM_KRYLOV_GMRES && o.krylov_max > 1000) ||
+            (o.krylov == SVM_KRYLOV_GMRES && o.krylov_max > 1000) || (o.autotune != 0 && o.autotune != 1) ||
             !(o.gamma > 0 && o.gamma < 1) || !(o.krylov_tol > 0) || !(o.ell > 0))
             return fail(ANOVA_ERR_INVALID_ARG, "invalid svm_opts");
         bool has_pos = false, has_neg = false;
@@ -875,11 +879,16 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         std::vector<double> ell(std::max(P, 1), o.ell);
         anova_plan *p32 = nullptr, *p64 = nullptr;
         anova_status s;
-        if ((s = create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32, o.cuda_stream, &p32)) != ANOVA_OK)
+        if ((s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32,
+                                        o.cuda_stream, 1, 3, nullptr, &p32)
+                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32,
+                                          o.cuda_stream, &p32)) != ANOVA_OK)
             return s;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g32(p32, destroy_plan);
-        if ((s = create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise, ANOVA_FP64,
-                             o.cuda_stream, &p64)) != ANOVA_OK)
+        if ((s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise,
+                                        ANOVA_FP64, o.cuda_stream, 1, 3, nullptr, &p64)
+                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise,
+                                          ANOVA_FP64, o.cuda_stream, &p64)) != ANOVA_OK)
             return s;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64(p64, destroy_plan);
         lowrank *lr = nullptr;

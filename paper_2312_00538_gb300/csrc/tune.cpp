@@ -1,0 +1,193 @@
+// Plan autotuner: builds the fast-summation plan (Sec. 3) under several launch settings and keeps
+// the fastest. The settings change only how the work is cut and scheduled, never the arithmetic of
+// a single point-window product, so every candidate computes the same K v up to the order of
+// floating-point sums.
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "anova_internal.h"
+
+namespace anova {
+anova_status fail(anova_status st, const std::string &msg);
+anova_status cuda_fail(cudaError_t e, const char *what);
+anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                         const double *ell, const double *eta, int N, int m, int flags, void *stream,
+                         anova_plan_t *out);
+
+namespace {
+
+struct Setting {
+    int interp, rhs_chunk, fork;
+};
+
+void apply(anova_plan *p, const Setting &s) {
+    p->interp_flags = s.interp;
+    p->rhs_chunk = s.rhs_chunk;
+    p->fork_windows = s.fork;
+}
+
+// Mean milliseconds of one matvec with nrhs columns over `reps` back-to-back calls after one
+// warm-up call, CUDA events on the plan's stream.
+anova_status time_matvec(anova_plan *p, const void *v, void *kv, int nrhs, int reps, double *ms) {
+    cudaStream_t st = p->stream;
+    auto run = [&]() {
+        return p->prec == ANOVA_FP64 ? run_matvec_t<double>(p, v, kv, nrhs, -1)
+                                     : run_matvec_t<float>(p, v, kv, nrhs, -1);
+    };
+    anova_status s = run();
+    if (s != ANOVA_OK) return s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return fail(ANOVA_ERR_CUDA, "cudaEventCreate");
+    }
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev{a, b};
+    ANOVA_CUDA_TRY(cudaEventRecord(a, st));
+    for (int r = 0; r < reps; ++r)
+        if ((s = run()) != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaEventRecord(b, st));
+    ANOVA_CUDA_TRY(cudaEventSynchronize(b));
+    float t = 0.0f;
+    ANOVA_CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+    // a kernel whose bounded wait ran out leaves its status word set
+    int status = 0;
+    ANOVA_CUDA_TRY(cudaMemcpy(&status, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) return fail(ANOVA_ERR_TIMEOUT, "a kernel wait ran out while tuning");
+    *ms = (double)t / reps;
+    return ANOVA_OK;
+}
+
+}  // namespace
+
+anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *windows, int P, const double *ell,
+                       const double *eta, int N, int m, int flags, void *stream, int nrhs, int reps,
+                       anova_tune_report *report, anova_plan_t *out) {
+    if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nrhs < 1 || nrhs > 1024) return fail(ANOVA_ERR_INVALID_ARG, "nrhs must be in [1, 1024]");
+    if (reps < 1 || reps > 1000) return fail(ANOVA_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    // the default plan first: it validates the arguments and gives the baseline time
+    anova_plan_t best = nullptr;
+    anova_status s = create_plan(points, n, d, windows, P, ell, eta, N, m, flags, stream, &best);
+    if (s != ANOVA_OK) return s;
+    struct Owned {
+        anova_plan *p = nullptr;
+        ~Owned() {
+            if (p) destroy_plan(p);
+        }
+    } best_owner{best}, cand_owner;
+    const bool fp64 = best->prec == ANOVA_FP64;
+    const size_t bytes = (fp64 ? 8 : 4) * (size_t)n * nrhs;
+    void *v = nullptr, *kv = nullptr;
+    if (cudaMalloc(&v, bytes) != cudaSuccess || cudaMalloc(&kv, bytes) != cudaSuccess) {
+        if (v) cudaFree(v);
+        return fail(ANOVA_ERR_OOM, "tuning buffers");
+    }
+    struct Free {
+        void *a, *b;
+        ~Free() {
+            cudaFree(a);
+            cudaFree(b);
+        }
+    } free_bufs{v, kv};
+    {
+        // deterministic, roughly centred values (the time does not depend on them)
+        std::vector<char> h(bytes);
+        uint64_t z = 0x2312005380000001ull;
+        const size_t cnt = (size_t)n * nrhs;
+        for (size_t i = 0; i < cnt; ++i) {
+            z = z * 6364136223846793005ull + 1442695040888963407ull;
+            const double x = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+            if (fp64) reinterpret_cast<double *>(h.data())[i] = x;
+            else reinterpret_cast<float *>(h.data())[i] = (float)x;
+        }
+        ANOVA_CUDA_TRY(cudaMemcpy(v, h.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    // settings: interpolation form where the plan has two, RHS per pass, FP64 window streams
+    bool two_interp = !fp64 && m == 4 && !(flags & (ANOVA_INTERP_TENSOR | ANOVA_INTERP_SIMT));
+    if (two_interp) {
+        bool has3 = false;
+        for (const WindowInfo &w : best->win) has3 = has3 || w.dw == 3;
+        two_interp = has3;
+    }
+    std::vector<int> interps = two_interp ? std::vector<int>{ANOVA_INTERP_TENSOR, ANOVA_INTERP_SIMT}
+                                          : std::vector<int>{flags & 6};
+    std::vector<int> chunks{std::min(nrhs, 16)};
+    for (int c : {8, 4})
+        if (c < nrhs && c < chunks[0]) chunks.push_back(c);
+    std::vector<int> forks = fp64 && P >= 2 ? std::vector<int>{1, 0} : std::vector<int>{1};
+    const Setting def{flags & 6, 16, 1};
+    int candidates = 0;
+    // best setting of one plan; the first timing is the default setting
+    auto search = [&](anova_plan *pl, Setting *set, double *ms_out) -> anova_status {
+        double bm = 0.0;
+        for (int it : interps)
+            for (int ch : chunks)
+                for (int fk : forks) {
+                    const Setting st{it, ch, fk};
+                    apply(pl, st);
+                    double ms = 0.0;
+                    anova_status r = time_matvec(pl, v, kv, nrhs, reps, &ms);
+                    if (r != ANOVA_OK) return r;
+                    ++candidates;
+                    if (bm == 0.0 || ms < bm) {
+                        bm = ms;
+                        *set = st;
+                    }
+                }
+        *ms_out = bm;
+        return ANOVA_OK;
+    };
+    double def_ms = 0.0, best_ms = 0.0;
+    apply(best, def);
+    if ((s = time_matvec(best, v, kv, nrhs, reps, &def_ms)) != ANOVA_OK) return s;
+    ++candidates;
+    Setting best_set = def;
+    if ((s = search(best, &best_set, &best_ms)) != ANOVA_OK) return s;
+    if (def_ms < best_ms) {
+        best_ms = def_ms;
+        best_set = def;
+    }
+    // other work-item caps need their own plan tables
+    for (int wi_max : {kWiMax / 2, kWiMax * 2}) {
+        anova_plan_t c = nullptr;
+        if ((s = create_plan_wi(points, n, d, windows, P, ell, eta, N, m, flags, stream, wi_max, &c)) != ANOVA_OK)
+            return s;
+        cand_owner.p = c;
+        Setting cs = def;
+        double cms = 0.0;
+        if ((s = search(c, &cs, &cms)) != ANOVA_OK) return s;
+        if (cms < best_ms) {
+            destroy_plan(best);
+            best = c;
+            best_owner.p = c;
+            best_set = cs;
+            best_ms = cms;
+        } else {
+            destroy_plan(c);
+        }
+        cand_owner.p = nullptr;
+    }
+    apply(best, best_set);
+    if (report) {
+        report->wi_max = best->wi_max;
+        report->interp = two_interp ? best_set.interp : 0;
+        report->rhs_chunk = std::min(best_set.rhs_chunk, nrhs);
+        report->fork_windows = fp64 && P >= 2 ? best_set.fork : 0;
+        report->candidates = candidates;
+        report->ms = best_ms;
+        report->ms_default = def_ms;
+    }
+    best_owner.p = nullptr;
+    *out = best;
+    return ANOVA_OK;
+}
+
+}  // namespace anova

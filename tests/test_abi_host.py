@@ -81,6 +81,11 @@ def test_invalid_arguments_are_rejected_before_any_device_work(ab):
             ab.anova_nfft_plan(**kw)
         assert ei.value.status == status, kw
     assert ab.anova_last_error() != ""
+    # the tuned plan validates its own arguments, then the plan's
+    for kw in (dict(nrhs=0), dict(nrhs=1025), dict(reps=0), dict(N=31)):
+        with pytest.raises(ab.AnovaError) as ei:
+            ab.anova_nfft_plan_tuned(X, W, 1.0, **kw)
+        assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG, kw
 
 
 def test_unused_features_may_lie_outside_the_box(ab):

@@ -80,12 +80,12 @@ def test_large_C_workload3_like(env, C):
     assert abs(d_gpu - d_ref) <= 1e-6 * abs(d_ref)
 
 
-@pytest.mark.parametrize("kind", ["random", "nystrom", "gmres", "per_window", "nystrom_random"])
+@pytest.mark.parametrize("kind", ["random", "nystrom", "gmres", "per_window", "nystrom_random", "autotune"])
 def test_other_preconditioners_reach_the_same_optimum(env, kind):
     """The optimum does not depend on the preconditioner or the Krylov method: randomly pivoted
     Cholesky, Nystrom (pivot set or orth(K G)), per-window stacked factors, and GMRES with the
     paper's block-triangular preconditioner (Sec. 5) reach the dense-KKT oracle's dual objective
-    on workload 1 (only iteration counts differ)."""
+    on workload 1 (only iteration counts differ); so do autotuned plans."""
     torch, ab = env
     cfg = config1()
     X, y, W, C = cfg["X"], cfg["y"], cfg["windows"], cfg["C"]
@@ -94,7 +94,9 @@ def test_other_preconditioners_reach_the_same_optimum(env, kind):
     o.krylov_tol = 1e-8
     o.max_iter = 100
     o.precond = {"random": ab.PCHOL_RANDOM, "nystrom": ab.NYSTROM, "gmres": ab.PCHOL_GREEDY,
-                 "per_window": ab.PCHOL_PER_WINDOW, "nystrom_random": ab.NYSTROM_RANDOM}[kind]
+                 "per_window": ab.PCHOL_PER_WINDOW, "nystrom_random": ab.NYSTROM_RANDOM,
+                 "autotune": ab.PCHOL_GREEDY}[kind]
+    o.autotune = 1 if kind == "autotune" else 0
     o.krylov = ab.SVM_KRYLOV_GMRES if kind == "gmres" else ab.SVM_KRYLOV_MINRES
     o.seed = 2023
     alpha, b, st, status = ab.svm_ipm_solve(X, y, C, 1e-6, opts=o, windows=W)

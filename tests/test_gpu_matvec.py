@@ -312,3 +312,37 @@ def test_tensor_and_simt_interpolation_agree(env):
             outs.append(_run(torch, ab, plan, v, torch.float32))
         for r in range(2):
             assert rel_l2(outs[0][:, r], outs[1][:, r]) <= 2e-6
+
+
+def test_tuned_plan_matches_default_and_oracle(env):
+    """The autotuned plan (work-item cap, interpolation form, RHS per pass, FP64 window streams)
+    computes the default plan's K v up to the order of sums, and the direct sum within the bar."""
+    torch, ab = env
+    X = _clustered(60000, SEED_BASE + 60)
+    X = np.column_stack([X, X[:, ::-1] * 0.9, np.roll(X, 1, axis=1)])
+    W = np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8]])
+    V = matvec_vectors(X.shape[0], 6, SEED_BASE + 61)
+    plan, rep = ab.anova_nfft_plan_tuned(X, W, 1.0, N=32, m=4, flags=ab.ANOVA_FP32, nrhs=6, reps=2)
+    assert rep["wi_max"] in (1024, 2048, 4096)
+    assert rep["interp"] in (ab.ANOVA_INTERP_TENSOR, ab.ANOVA_INTERP_SIMT)
+    assert rep["rhs_chunk"] in (6, 4) and rep["candidates"] == 1 + 3 * 2 * 2
+    assert 0 < rep["ms"] <= rep["ms_default"]
+    got = _run(torch, ab, plan, V, torch.float32)
+    ref_plan = ab.anova_nfft_plan(X, W, 1.0, N=32, m=4, flags=ab.ANOVA_FP32)
+    dflt = _run(torch, ab, ref_plan, V, torch.float32)
+    idx = subsample_rows(X.shape[0], 800, SEED_BASE + 62)
+    ref = ok.anova_matvec(X, W, 1.0, V[:, :2], rows=idx)
+    for r in range(6):
+        assert rel_l2(got[:, r], dflt[:, r]) <= 2e-6
+    for r in range(2):
+        assert rel_l2(got[idx, r], ref[:, r]) <= FP32_BAR
+    # FP64: the window streams are searched too
+    cfg = config1()
+    V2 = matvec_vectors(2000, 2, SEED_BASE + 63)
+    p64, rep64 = ab.anova_nfft_plan_tuned(cfg["X"], cfg["windows"], cfg["sigma"], N=64, m=6,
+                                          flags=ab.ANOVA_FP64, nrhs=2, reps=2)
+    assert rep64["interp"] == 0 and rep64["fork_windows"] in (0, 1) and rep64["candidates"] == 1 + 3 * 2
+    got64 = _run(torch, ab, p64, V2, torch.float64)
+    ref64 = ok.anova_matvec(cfg["X"], cfg["windows"], cfg["sigma"], V2)
+    for r in range(2):
+        assert rel_l2(got64[:, r], ref64[:, r]) <= FP64_BAR

@@ -27,9 +27,10 @@ def test_defaults_follow_table1(ab):
     assert o.stop == ab.SVM_STOP_GAP
     assert (o.N, o.m, o.N_precise, o.m_precise) == (32, 4, 64, 6)
     assert o.krylov == ab.SVM_KRYLOV_MINRES
+    assert o.autotune == 0
 
 
-@pytest.mark.parametrize("case", ["labels", "one_class", "C", "tol", "opts", "krylov"])
+@pytest.mark.parametrize("case", ["labels", "one_class", "C", "tol", "opts", "krylov", "autotune"])
 def test_invalid_solver_arguments(ab, case):
     X = np.zeros((6, 3))
     y = np.array([1.0, -1.0, 1.0, -1.0, 1.0, -1.0])
@@ -48,6 +49,8 @@ def test_invalid_solver_arguments(ab, case):
         o.sigma_barrier = 1.5
     if case == "krylov":
         o.krylov = 7
+    if case == "autotune":
+        o.autotune = 2
     with pytest.raises(ab.AnovaError) as ei:
         ab.svm_ipm_solve(X, y, C, tol, opts=o)
     assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
