@@ -106,6 +106,7 @@ struct anova_plan {
     int4 *segs = nullptr;         // {cell packed, sorted start, count, window}
     int4 *wis = nullptr;          // {window, seg_begin, seg_end, tile origin packed}
     int *wi_order = nullptr;      // per window: its work items by decreasing point count
+    int *wi_gorder = nullptr;     // per dimension group: all its work items by decreasing point count
     int2 *bins = nullptr;         // per window per bin: {first work item, count}
     int4 *mbins = nullptr;        // multi-item bins: {first work item, count, tile volume, 0}
     int nmbins = 0;

@@ -12,8 +12,16 @@ namespace anova {
 #ifndef ANOVA_SPREAD_WARPS
 #define ANOVA_SPREAD_WARPS 8  // warps per CTA of the packed FP32 spread
 #endif
-constexpr int kTcMinPointsPerItem = 512;
-constexpr int kAuxStreams = 3;  // concurrent window chains of one matvec  // mean points per work item for the tensor-core form
+// Work order knobs, both off: measured at n = 1e6 (three 3-D windows), largest-first spread CTAs
+// made the spread 2 % slower and the group-wide order changed the interpolation by under 1 %.
+#ifndef ANOVA_SPREAD_ORDER
+#define ANOVA_SPREAD_ORDER 0  // packed spread: CTAs take work items largest first
+#endif
+#ifndef ANOVA_GROUP_ORDER
+#define ANOVA_GROUP_ORDER 0   // largest-first order over a whole dimension group (else per window)
+#endif
+constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core form
+constexpr int kAuxStreams = 3;           // concurrent window chains of one matvec
 #ifndef ANOVA_INTERP_VARIANT
 // FP32 3-D interpolation with m = 4: 2 = tensor cores where chosen, 0 = always one point per lane
 #define ANOVA_INTERP_VARIANT 2
@@ -392,6 +400,10 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         sa.wi_begin = wi0;
         sa.wi_end = wi1;
         sa.wp = wp;
+        // largest work items first: over the whole group when the launch covers it
+        const bool whole_group = a0 == gr.w_begin && a1 == gr.w_end;
+        const int *order = whole_group && ANOVA_GROUP_ORDER ? p->wi_gorder : p->wi_order;
+        sa.order = ANOVA_SPREAD_ORDER ? order : nullptr;
         if (wi1 > wi0) {
             cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "spread launch");
@@ -467,7 +479,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
             xa.wp = wp;
             xa.status = p->dev_status;
             xa.counters = counters;
-            xa.order = p->wi_order;
+            xa.order = order;
             cudaError_t e;
             // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
             // points; it is used when work items are well filled (large n), else the SIMT form

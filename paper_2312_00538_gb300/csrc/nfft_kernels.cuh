@@ -40,6 +40,7 @@ struct SpreadArgs {
     long long n, total;
     int nrhs, wi_begin, wi_end;
     WinParams wp;
+    const int *order;       // packed kernel: CTA k takes work item order[wi_begin + k] (null: identity)
 };
 
 template <typename T, int DW, int M, int B, int NWARP>
@@ -215,8 +216,8 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
     float *tiles_s = reinterpret_cast<float *>(smem_raw);
     float *wts_s = tiles_s + NWARP * C::TVP;
 
-    const int wi_idx = a.wi_begin + blockIdx.x;
-    if (wi_idx >= a.wi_end) return;
+    if (a.wi_begin + (int)blockIdx.x >= a.wi_end) return;
+    const int wi_idx = a.order ? a.order[a.wi_begin + blockIdx.x] : a.wi_begin + blockIdx.x;
     const int r = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = lane / LPP, lh = lane % LPP;

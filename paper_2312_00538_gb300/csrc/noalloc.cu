@@ -51,6 +51,7 @@ anova_status spread_noalloc(anova_plan *p, int w, const void *v, void *grid) {
 
     SpreadArgs sa;
     sa.packed = 0;  // the generic spread kernel
+    sa.order = nullptr;
     sa.wis = p->wis;
     sa.segs = p->segs;
     sa.frac = p->frac;

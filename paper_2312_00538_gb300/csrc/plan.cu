@@ -223,7 +223,7 @@ void destroy_plan(anova_plan *p) {
     }
     if (p->fork_evt) cudaEventDestroy(p->fork_evt);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->bins, p->mbins, p->ftiles, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -651,6 +651,19 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
             for (int i = 0; i < b1 - b0; ++i) order[b0 + i] = sz[i].second;
         }
         if ((s = upload((void **)&p->wi_order, order.data(), sizeof(int) * order.size())) != ANOVA_OK) return s;
+        // the same over each dimension group (launches that cover a whole group)
+        for (const Group &gr : p->groups) {
+            std::vector<std::pair<int, int>> sz;
+            sz.reserve(gr.wi_end - gr.wi_begin);
+            for (int x = gr.wi_begin; x < gr.wi_end; ++x) {
+                int cnt = 0;
+                for (int sgi = wis[x].y; sgi < wis[x].z; ++sgi) cnt += segs[sgi].z;
+                sz.emplace_back(-cnt, x);
+            }
+            std::sort(sz.begin(), sz.end());
+            for (int i = 0; i < gr.wi_end - gr.wi_begin; ++i) order[gr.wi_begin + i] = sz[i].second;
+        }
+        if ((s = upload((void **)&p->wi_gorder, order.data(), sizeof(int) * order.size())) != ANOVA_OK) return s;
     }
     if ((s = upload((void **)&p->bins, bins.data(), sizeof(int2) * bins.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->mbins, mbins.data(), sizeof(int4) * mbins.size())) != ANOVA_OK) return s;
