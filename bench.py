@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study", "predict"],
                     help="matvec (default, the headline line) or ipm_batch (independent SVM "
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
@@ -526,6 +526,59 @@ def run_precond_study(args):
     return 0
 
 
+def run_predict(args):
+    """Prediction (targets distinct from the sources, Sec. 6) on the matvec workload's points:
+    n sources with weights w, n fresh targets from the same generator. Times, with CUDA events and
+    inputs resident, (a) anova_cross_matvec per call, (b) anova_model_create once, and (c)
+    anova_model_eval per call; the value is target points per second of (c)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import matvec_vectors
+    n = args.n
+    Xs, W, vseed = workload(n)
+    Xt = workload(n, seed_offset=1)[0]
+    w = torch.tensor(matvec_vectors(n, 1, vseed)[:, 0], dtype=torch.float32, device="cuda")
+    src = ab.anova_nfft_plan(Xs, W, args.sigma, N=32, m=4)
+    tgt = ab.anova_nfft_plan(Xt, W, args.sigma, N=32, m=4)
+    f = torch.empty(n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps):
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    for _ in range(max(3, args.warmup)):
+        ab.anova_cross_matvec(src, tgt, w, f)
+    cross_ms = timed(lambda: ab.anova_cross_matvec(src, tgt, w, f), args.steps)
+    f_cross = f.clone()
+    models = []
+    create_ms = timed(lambda: models.append(ab.anova_model_create(src, w)), 3)
+    model = models[-1]
+    for _ in range(max(3, args.warmup)):
+        ab.anova_model_eval(model, tgt, f)
+    eval_ms = timed(lambda: ab.anova_model_eval(model, tgt, f), args.steps)
+    rel = float(torch.linalg.vector_norm((f - f_cross).double()) / torch.linalg.vector_norm(f_cross.double()))
+    print(json.dumps({
+        "metric": "ANOVA-NFFT prediction (targets != sources) target points/s", "value": n / (eval_ms / 1e3),
+        "unit": "target_points/s", "ms_per_step": eval_ms, "steps": args.steps, "higher_is_better": True,
+        "data": "synthetic", "dtype": "f32",
+        "config": {"workload": "prediction n_source=%d n_target=%d d=9 windows=3x3D sigma=%g N=32 m=4"
+                               % (n, n, args.sigma), "l2": "flushed between steps (512 MiB write)"},
+        "cross_matvec_ms": cross_ms, "model_create_ms": create_ms, "model_eval_ms": eval_ms,
+        "model_vs_cross_rel_l2": rel}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -536,6 +589,8 @@ def main():
         return run_serve(args)
     if args.workload == "precond_study":
         return run_precond_study(args)
+    if args.workload == "predict":
+        return run_predict(args)
     return run_ours(args)
 
 

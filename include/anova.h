@@ -183,6 +183,27 @@ anova_status anova_spread_grid_noalloc(anova_plan_t plan, int l, const void *v, 
 anova_status anova_cross_matvec(anova_plan_t source, anova_plan_t target, const void *w, void *f);
 
 /*
+ * Prediction with the source half kept (Sec. 6: the decision function is evaluated at many new
+ * points for one trained alpha). anova_cross_matvec redoes the spread and the full convolution of
+ * the sources on every call; a model does them once.
+ * anova_model_create -- spreads w (device, n_source values of the plan's precision) with
+ *   `source`'s plan and convolves every window's grid in full (FFT, scaling, inverse FFT); the
+ *   model keeps the convolved grids (n_os^{d_l} values per window, on the plan's device) and
+ *   copies of the plan's window parameters, so the plan and w may be released afterwards.
+ *   Synchronises the plan's stream. Errors: INVALID_ARG (NULL), OOM, CUDA.
+ * anova_model_eval -- f_j = sum_l eta_l sum_i w_i exp(-||t_j^{W_l} - s_i^{W_l}||^2 / ell_l^2) at
+ *   the target plan's points (device, n_target values, overwritten): the target plan's
+ *   interpolation from the kept grids, then the window sum. The target plan must match the model
+ *   as anova_cross_matvec's plans must match (else INVALID_ARG). Asynchronous on the target plan's
+ *   stream, like anova_matvec; results equal anova_cross_matvec's up to the order of sums.
+ * anova_model_destroy -- frees the grids (NULL is ignored).
+ */
+typedef struct anova_model *anova_model_t;
+anova_status anova_model_create(anova_plan_t source, const void *w, anova_model_t *out);
+anova_status anova_model_eval(anova_model_t model, anova_plan_t target, void *f);
+void anova_model_destroy(anova_model_t model);
+
+/*
  * anova_nfft_plan_tuned -- anova_nfft_plan_ex (same arguments and errors) followed by a search
  * over launch settings that leave the arithmetic of each point-window product unchanged; the
  * fastest plan is returned. Settings: the points-per-work-item cap of the spread/interpolation

@@ -63,6 +63,9 @@ _SIGNATURES = {
     "anova_nfft_plan_tuned": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _dp, _dp, _c_int, _c_int,
                                        _c_int, _vp, _c_int, _c_int, _vp, ctypes.POINTER(_vp)]),
     "anova_matvec": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "anova_model_create": (_c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "anova_model_eval": (_c_int, [_vp, _vp, _vp]),
+    "anova_model_destroy": (None, [_vp]),
     "anova_matvec_host": (_c_int, [_vp, _vp, _vp, _c_int]),
     "anova_window_matvec": (_c_int, [_vp, _c_int, _vp, _vp]),
     "anova_spread_grid": (_c_int, [_vp, _c_int, _vp, _vp]),
@@ -292,6 +295,37 @@ def anova_plan_info(plan):
 def anova_cross_matvec(source, target, w, f):
     """f (device, target points) = sum over windows and sources of w_i K(t_j, s_i)."""
     _check(lib().anova_cross_matvec(source.handle, target.handle, _dev_ptr(w), _dev_ptr(f)))
+
+
+class Model:
+    """Owns an anova_model_t (the kept, convolved source grids); destroyed with the object."""
+
+    def __init__(self, handle, precision):
+        self.handle = handle
+        self.precision = precision
+
+    def destroy(self):
+        if self.handle:
+            lib().anova_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def anova_model_create(source, w):
+    """Spreads and convolves the weights w (device tensor, source points) once."""
+    h = _vp()
+    _check(lib().anova_model_create(source.handle, _dev_ptr(w), ctypes.byref(h)))
+    return Model(h, source.precision)
+
+
+def anova_model_eval(model, target, f):
+    """f (device, target points) from the model's kept grids."""
+    _check(lib().anova_model_eval(model.handle, target.handle, _dev_ptr(f)))
 
 
 def anova_plan_check(plan):

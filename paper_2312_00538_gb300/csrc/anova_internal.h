@@ -149,6 +149,15 @@ struct anova_plan {
     int64_t launches = 0;          // kernels launched since the last timing reset
 };
 
+// A kept source half of the cross product: every window's convolved grid for fixed weights w.
+struct anova_model {
+    int device = 0, prec = 0, N = 0, m = 0, P = 0;
+    std::vector<int> user_to_internal;
+    std::vector<anova::WindowInfo> win;  // the source plan's windows (dw, ell, eta, grid_off used)
+    long long grid_total = 0;
+    void *grid = nullptr;                // T[grid_total]
+};
+
 namespace anova {
 enum { STAGE_SPREAD = 0, STAGE_REDUCE = 1, STAGE_FFT = 2, STAGE_INTERP = 3, STAGE_SUM = 4, NUM_STAGES = 5 };
 // Records a CUDA event on the plan's stream when timing is on; returns the event (or null).
@@ -168,6 +177,12 @@ template <typename T>
 anova_status run_interp_grid_t(anova_plan *p, int w, const void *grid, void *f);
 template <typename T>
 anova_status run_cross_matvec_t(anova_plan *src, anova_plan *tgt, const void *w, void *f);
+// Source half into model->grid (allocated by the caller, grid_total elements); synchronises.
+template <typename T>
+anova_status run_model_create_t(anova_plan *src, const void *w, anova_model *model);
+// Target half: interpolation at tgt's points from the model's grids, then the window sum.
+template <typename T>
+anova_status run_model_eval_t(const anova_model *model, anova_plan *tgt, void *f);
 // create_plan with an explicit work-item cap (kSegMax <= wi_max <= 1 << 16)
 anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_t *windows, int P,
                             const double *ell, const double *eta, int N, int m, int flags, void *stream,

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -260,6 +261,65 @@ anova_status anova_cross_matvec(anova_plan_t source, anova_plan_t target, const 
         if (source->prec == ANOVA_FP64) return run_cross_matvec_t<double>(source, target, w, f);
         return run_cross_matvec_t<float>(source, target, w, f);
     });
+}
+
+anova_status anova_model_create(anova_plan_t source, const void *w, anova_model_t *out) {
+    return guarded([&]() -> anova_status {
+        if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+        *out = nullptr;
+        if (!source) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!w) return fail(ANOVA_ERR_INVALID_ARG, "w is NULL");
+        DeviceGuard g(source->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        std::unique_ptr<anova_model> m(new anova_model());
+        m->device = source->device;
+        m->prec = source->prec;
+        m->N = source->N;
+        m->m = source->m;
+        m->P = source->P;
+        m->user_to_internal = source->user_to_internal;
+        m->win = source->win;
+        m->grid_total = source->grid_total;
+        ANOVA_CUDA_TRY(cudaMalloc(&m->grid, elem_size(source) * (size_t)source->grid_total));
+        const anova_status st = source->prec == ANOVA_FP64 ? run_model_create_t<double>(source, w, m.get())
+                                                           : run_model_create_t<float>(source, w, m.get());
+        if (st != ANOVA_OK) {
+            cudaFree(m->grid);
+            return st;
+        }
+        *out = m.release();
+        return ANOVA_OK;
+    });
+}
+
+anova_status anova_model_eval(anova_model_t model, anova_plan_t target, void *f) {
+    return guarded([&]() -> anova_status {
+        if (!model || !target) return fail(ANOVA_ERR_INVALID_ARG, "model or plan is NULL");
+        if (!f) return fail(ANOVA_ERR_INVALID_ARG, "f is NULL");
+        if (model->device != target->device) return fail(ANOVA_ERR_INVALID_ARG, "model and plan on different devices");
+        if (model->prec != target->prec || model->N != target->N || model->m != target->m || model->P != target->P ||
+            model->user_to_internal != target->user_to_internal || model->grid_total != target->grid_total)
+            return fail(ANOVA_ERR_INVALID_ARG, "model and target plan differ in precision, N, m or windows");
+        for (int k = 0; k < model->P; ++k) {
+            const WindowInfo &a = model->win[k], &b = target->win[k];
+            if (a.dw != b.dw || a.ell != b.ell || a.eta != b.eta || a.grid_off != b.grid_off)
+                return fail(ANOVA_ERR_INVALID_ARG, "model and target plan differ in a window's dimension, ell or eta");
+        }
+        DeviceGuard g(target->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        if (target->prec == ANOVA_FP64) return run_model_eval_t<double>(model, target, f);
+        return run_model_eval_t<float>(model, target, f);
+    });
+}
+
+void anova_model_destroy(anova_model_t model) {
+    if (!model) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != model->device) cudaSetDevice(model->device);
+    cudaFree(model->grid);
+    if (prev >= 0 && prev != model->device) cudaSetDevice(prev);
+    delete model;
 }
 
 anova_status anova_plan_check(anova_plan_t plan) {

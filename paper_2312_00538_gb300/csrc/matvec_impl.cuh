@@ -372,6 +372,100 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
     return ANOVA_OK;
 }
 
+// Stage 4 of one group's windows [a0, a1): interpolation from the convolved grids `grid` (the
+// layout of the plan's grid workspace) into the per-window results `part`.
+template <typename T>
+anova_status interp_stage(anova_plan *p, const Group &gr, int a0, int a1, int w0, const T *grid,
+                          long long grid_stride, int nrhs, T *part, const WinParams &wp, cudaStream_t st,
+                          int *counters) {
+    const int wi0 = p->win[a0].wi_begin, wi1 = p->win[a1 - 1].wi_end;
+    const int s0 = p->win[a0].seg_begin, s1 = p->win[a1 - 1].seg_end;
+    const bool packed = packed_path((int)sizeof(T), gr.dw, p->m);
+    const bool whole_group = a0 == gr.w_begin && a1 == gr.w_end;
+    const int *order = whole_group && ANOVA_GROUP_ORDER ? p->wi_gorder : p->wi_order;
+    if (packed && wi1 > wi0) {
+        InterpWiArgs xa;
+        xa.wis = p->wis;
+        xa.segs = p->segs;
+        xa.frac = reinterpret_cast<const float *>(p->frac);
+        xa.perm = p->perm;
+        xa.cellloc = p->cellloc;
+        xa.grid = reinterpret_cast<const float *>(grid);
+        xa.dwin = p->dwin;
+        xa.part = reinterpret_cast<float *>(part);
+        xa.n = p->n;
+        xa.total = p->n * p->P;
+        xa.grid_stride_rhs = grid_stride;
+        xa.nrhs = nrhs;
+        xa.wi_begin = wi0;
+        xa.wi_end = wi1;
+        xa.n_os = p->n_os;
+        xa.part_w0 = w0;
+        xa.wp = wp;
+        xa.status = p->dev_status;
+        xa.counters = counters;
+        xa.order = order;
+        cudaError_t e;
+        // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
+        // points; it is used when work items are well filled (large n), else the SIMT form
+        const bool tc_fill = (p->interp_flags & ANOVA_INTERP_TENSOR) ||
+                             (!(p->interp_flags & ANOVA_INTERP_SIMT) &&
+                              (double)p->n * (a1 - a0) >= (double)kTcMinPointsPerItem * (wi1 - wi0));
+        if (p->m == 4)
+            e = ANOVA_INTERP_VARIANT == 2 && tc_fill ? launch_interp3_tc<4>(xa, wi1 - wi0, nrhs, p->sm_count, st)
+                                                     : launch_interp3_x2<4>(xa, wi1 - wi0, nrhs, st);
+        else
+            e = launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
+        if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+        p->launches += 1;
+    } else if (sizeof(T) == 8 && s1 > s0) {
+        InterpDirectArgs<T> da;
+        da.frac = reinterpret_cast<const T *>(p->frac);
+        da.perm = p->perm;
+        da.segs = p->segs;
+        da.grid = grid;
+        da.dwin = p->dwin;
+        da.part = part;
+        da.n = p->n;
+        da.total = p->n * p->P;
+        da.grid_stride_rhs = grid_stride;
+        da.nrhs = nrhs;
+        da.seg_begin = s0;
+        da.seg_end = s1;
+        da.n_os = p->n_os;
+        da.part_w0 = w0;
+        da.q_begin = (long long)a0 * p->n;
+        da.q_end = (long long)a1 * p->n;
+        da.wp = wp;
+        cudaError_t e = dispatch_interp_direct<T>(gr.dw, p->m, da, nrhs, st);
+        if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+        p->launches += 1;
+    } else if (wi1 > wi0) {
+        InterpBinArgs<T> ba;
+        ba.wis = p->wis;
+        ba.segs = p->segs;
+        ba.frac = reinterpret_cast<const T *>(p->frac);
+        ba.perm = p->perm;
+        ba.cellloc = p->cellloc;
+        ba.grid = grid;
+        ba.dwin = p->dwin;
+        ba.part = part;
+        ba.n = p->n;
+        ba.total = p->n * p->P;
+        ba.grid_stride_rhs = grid_stride;
+        ba.nrhs = nrhs;
+        ba.wi_begin = wi0;
+        ba.wi_end = wi1;
+        ba.n_os = p->n_os;
+        ba.part_w0 = w0;
+        ba.wp = wp;
+        cudaError_t e = dispatch_interp_bin<T>(gr.dw, p->m, ba, wi1 - wi0, nrhs, st);
+        if (e != cudaSuccess) return cuda_fail(e, "interp launch");
+        p->launches += 1;
+    }
+    return ANOVA_OK;
+}
+
 // One matvec over the window range [w0, w1) (all groups intersecting it). `part` receives
 // per-window results in original point order; grids g[0..3] are the workspace buffers.
 template <typename T>
@@ -441,102 +535,9 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         cudaEvent_t e3 = stage_event(p);
         stage_record(p, STAGE_FFT, e2, e3);
         // 4. interpolation
-        InterpArgs ia;
-        ia.segs = p->segs;
-        ia.frac = p->frac;
-        ia.perm = p->perm;
-        ia.grid = g[3];
-        ia.dwin = p->dwin;
-        ia.part = part;
-        ia.n = p->n;
-        ia.total = p->n * p->P;
-        ia.grid_stride_rhs = grid_stride;
-        ia.nrhs = nrhs;
-        ia.seg_begin = s0;
-        ia.seg_end = s1;
-        ia.n_os = p->n_os;
-        ia.zero_offset = 0;
-        ia.part_w0 = w0;
-        ia.wp = wp;
-        if (packed && wi1 > wi0) {
-            InterpWiArgs xa;
-            xa.wis = p->wis;
-            xa.segs = p->segs;
-            xa.frac = reinterpret_cast<const float *>(p->frac);
-            xa.perm = p->perm;
-            xa.cellloc = p->cellloc;
-            xa.grid = reinterpret_cast<const float *>(g[3]);
-            xa.dwin = p->dwin;
-            xa.part = reinterpret_cast<float *>(part);
-            xa.n = p->n;
-            xa.total = p->n * p->P;
-            xa.grid_stride_rhs = grid_stride;
-            xa.nrhs = nrhs;
-            xa.wi_begin = wi0;
-            xa.wi_end = wi1;
-            xa.n_os = p->n_os;
-            xa.part_w0 = w0;
-            xa.wp = wp;
-            xa.status = p->dev_status;
-            xa.counters = counters;
-            xa.order = order;
-            cudaError_t e;
-            // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
-            // points; it is used when work items are well filled (large n), else the SIMT form
-            const bool tc_fill = (p->interp_flags & ANOVA_INTERP_TENSOR) ||
-                                 (!(p->interp_flags & ANOVA_INTERP_SIMT) &&
-                                  (double)p->n * (a1 - a0) >= (double)kTcMinPointsPerItem * (wi1 - wi0));
-            if (p->m == 4)
-                e = ANOVA_INTERP_VARIANT == 2 && tc_fill ? launch_interp3_tc<4>(xa, wi1 - wi0, nrhs, p->sm_count, st)
-                                                         : launch_interp3_x2<4>(xa, wi1 - wi0, nrhs, st);
-            else
-                e = launch_interp3_x2<2>(xa, wi1 - wi0, nrhs, st);
-            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
-            p->launches += 1;
-        } else if (sizeof(T) == 8 && s1 > s0) {
-            InterpDirectArgs<T> da;
-            da.frac = reinterpret_cast<const T *>(p->frac);
-            da.perm = p->perm;
-            da.segs = p->segs;
-            da.grid = g[3];
-            da.dwin = p->dwin;
-            da.part = part;
-            da.n = p->n;
-            da.total = p->n * p->P;
-            da.grid_stride_rhs = grid_stride;
-            da.nrhs = nrhs;
-            da.seg_begin = s0;
-            da.seg_end = s1;
-            da.n_os = p->n_os;
-            da.part_w0 = w0;
-            da.q_begin = (long long)a0 * p->n;
-            da.q_end = (long long)a1 * p->n;
-            da.wp = wp;
-            cudaError_t e = dispatch_interp_direct<T>(gr.dw, p->m, da, nrhs, st);
-            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
-            p->launches += 1;
-        } else if (wi1 > wi0) {
-            InterpBinArgs<T> ba;
-            ba.wis = p->wis;
-            ba.segs = p->segs;
-            ba.frac = reinterpret_cast<const T *>(p->frac);
-            ba.perm = p->perm;
-            ba.cellloc = p->cellloc;
-            ba.grid = g[3];
-            ba.dwin = p->dwin;
-            ba.part = part;
-            ba.n = p->n;
-            ba.total = p->n * p->P;
-            ba.grid_stride_rhs = grid_stride;
-            ba.nrhs = nrhs;
-            ba.wi_begin = wi0;
-            ba.wi_end = wi1;
-            ba.n_os = p->n_os;
-            ba.part_w0 = w0;
-            ba.wp = wp;
-            cudaError_t e = dispatch_interp_bin<T>(gr.dw, p->m, ba, wi1 - wi0, nrhs, st);
-            if (e != cudaSuccess) return cuda_fail(e, "interp launch");
-            p->launches += 1;
+        {
+            anova_status is = interp_stage<T>(p, gr, a0, a1, w0, g[3], grid_stride, nrhs, part, wp, st, counters);
+            if (is != ANOVA_OK) return is;
         }
         cudaEvent_t e4 = stage_event(p);
         stage_record(p, STAGE_INTERP, e3, e4);

@@ -62,3 +62,51 @@ def test_mismatched_plans_are_refused():
         with pytest.raises(ab.AnovaError) as ei:
             ab.anova_cross_matvec(a, other, vd, f)
         assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_kept_model_matches_cross_matvec_and_direct_sum(prec):
+    """A model keeps the sources' convolved grids: evaluating it at two target sets equals the
+    cross product (up to the order of sums) and the direct sum, after the source plan and the
+    weights are gone."""
+    torch, ab = require_gpu()
+    Xs = _points(4000, SEED_BASE + 77)
+    w = np.random.default_rng(SEED_BASE + 78).standard_normal(4000)
+    fl, dt, N, m, bar = ((ab.ANOVA_FP32, torch.float32, 32, 4, 1e-4) if prec == "fp32"
+                         else (ab.ANOVA_FP64, torch.float64, 64, 6, 1e-9))
+    src = ab.anova_nfft_plan(Xs, W, 0.8, N=N, m=m, flags=fl)
+    wd = to_dev(torch, w, dt)
+    model = ab.anova_model_create(src, wd)
+    targets = [_points(2100, SEED_BASE + 79), _points(900, SEED_BASE + 80)]
+    crossed = []
+    for Xt in targets:
+        tgt = ab.anova_nfft_plan(Xt, W, 0.8, N=N, m=m, flags=fl)
+        f = torch.empty(Xt.shape[0], dtype=dt, device="cuda")
+        ab.anova_cross_matvec(src, tgt, wd, f)
+        crossed.append(from_dev(f))
+    src.destroy()
+    del wd
+    for Xt, fc in zip(targets, crossed):
+        tgt = ab.anova_nfft_plan(Xt, W, 0.8, N=N, m=m, flags=fl)
+        f = torch.empty(Xt.shape[0], dtype=dt, device="cuda")
+        ab.anova_model_eval(model, tgt, f)
+        torch.cuda.synchronize()
+        ab.anova_plan_check(tgt)
+        got = from_dev(f)
+        assert rel_l2(got, fc) <= (2e-6 if prec == "fp32" else 1e-12)
+        assert rel_l2(got, ok.anova_cross_matvec(Xs, Xt, W, 0.8, w)) <= bar
+    model.destroy()
+
+
+def test_kept_model_refuses_mismatched_plans():
+    torch, ab = require_gpu()
+    X = _points(300, SEED_BASE + 81)
+    src = ab.anova_nfft_plan(X, W, 0.8, N=32, m=4)
+    model = ab.anova_model_create(src, torch.ones(300, device="cuda"))
+    f = torch.empty(300, device="cuda")
+    for other in (ab.anova_nfft_plan(X, W, 0.9, N=32, m=4), ab.anova_nfft_plan(X, W, 0.8, N=32, m=3),
+                  ab.anova_nfft_plan(X, W[:2], 0.8, N=32, m=4),
+                  ab.anova_nfft_plan(X, W, 0.8, N=64, m=6, flags=ab.ANOVA_FP64)):
+        with pytest.raises(ab.AnovaError) as ei:
+            ab.anova_model_eval(model, other, f)
+        assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
