@@ -20,6 +20,10 @@ constexpr int kSegMax = 256;           // points per segment (one cell, split at
 #define ANOVA_WI_MAX 2048
 #endif
 constexpr int kWiMax = ANOVA_WI_MAX;  // points per spread work item (at most)
+#ifndef ANOVA_F64_B
+#define ANOVA_F64_B 4
+#endif
+constexpr int kBinF64 = ANOVA_F64_B;   // cells per bin edge of FP64 plans (FP32: 4)
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;

@@ -64,6 +64,40 @@ struct Weights<double, M> {
     }
 };
 
+// One pair of window weights, lo = psi(f + M - 1 - j) and hi = psi(f - M + j), from the
+// even/odd coefficients cj[0..D] of pair j (D = kPolyDeg or kPolyDeg64); the same operations in
+// the same order as Weights<T, M>::eval, so both give identical values.
+template <typename T, int D>
+__device__ __forceinline__ void window_pair(T f, const T *cj, T &lo, T &hi) {
+    const T z = fma(T(2), f, T(-1));
+    const T z2 = z * z;
+    T e = cj[D - 1], o = cj[D];
+#pragma unroll
+    for (int p = D - 3; p >= 0; p -= 2) {
+        e = fma(e, z2, cj[p]);
+        o = fma(o, z2, cj[p + 1]);
+    }
+    lo = fma(z, o, e);
+    hi = fma(-z, o, e);
+}
+
+template <typename T>
+struct PolyDegOf {
+    static constexpr int D = kPolyDeg;
+};
+template <>
+struct PolyDegOf<double> {
+    static constexpr int D = kPolyDeg64;
+};
+
+// Coefficient j, p of the window polynomials of type T.
+template <typename T>
+__device__ __forceinline__ T window_coef(const WinParams &wp, int j, int p);
+template <>
+__device__ __forceinline__ float window_coef<float>(const WinParams &wp, int j, int p) { return wp.c[j][p]; }
+template <>
+__device__ __forceinline__ double window_coef<double>(const WinParams &wp, int j, int p) { return wp.c64[j][p]; }
+
 __device__ __forceinline__ int cell_coord(int packed, int k) { return (packed >> (10 * k)) & 1023; }
 
 // ---------------------------------------------------------------- packed FP32 pairs (f32x2)

@@ -38,10 +38,13 @@ struct Prec<float> {
     static constexpr int SPREAD_WARPS = ANOVA_SPREAD_WARPS;
     static constexpr int INTERP_WARPS = 8;
 };
+#ifndef ANOVA_F64_SPREAD_WARPS
+#define ANOVA_F64_SPREAD_WARPS 4
+#endif
 template <>
 struct Prec<double> {
-    static constexpr int B = 2;
-    static constexpr int SPREAD_WARPS = 4;
+    static constexpr int B = kBinF64;
+    static constexpr int SPREAD_WARPS = ANOVA_F64_SPREAD_WARPS;
     static constexpr int INTERP_WARPS = 4;
 };
 

@@ -49,7 +49,10 @@ struct SpreadCfg {
     static constexpr int TW = B + 2 * M - 1;
     static constexpr int TV = ipow(TW, DW);
     static constexpr int TVP = (TV + 3) / 4 * 4;
-    static constexpr size_t smem = sizeof(T) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * G::PSTRIDE);
+    static constexpr int CS = 16;  // coefficients per window pair in shared memory (>= degree + 1)
+    // warp tiles, staged weights, window coefficients
+    static constexpr size_t smem =
+        sizeof(T) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * G::PSTRIDE + (size_t)M * CS);
 };
 
 template <typename T, int DW, int M, int B, int NWARP>
@@ -58,9 +61,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
     using G = typename C::G;
     constexpr int W2 = G::W2, RPL = G::RPL, WS = G::WS, PS = G::PSTRIDE, TW = C::TW;
     constexpr int RCH = RPL < 2 ? RPL : 2;  // rows per lane held in registers at once
+    constexpr int PD = PolyDegOf<T>::D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tiles_s = reinterpret_cast<T *>(smem_raw);
     T *wts_s = tiles_s + NWARP * C::TVP;
+    T *coef_s = wts_s + NWARP * 32 * PS;
 
     const int wi_idx = a.wi_begin + blockIdx.x;
     if (wi_idx >= a.wi_end) return;
@@ -71,6 +76,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
     int bin[3] = {cell_coord(bin_packed, 0), cell_coord(bin_packed, 1), cell_coord(bin_packed, 2)};
 
     for (int i = threadIdx.x; i < NWARP * C::TVP; i += NWARP * 32) tiles_s[i] = T(0);
+    for (int i = threadIdx.x; i < M * (PD + 1); i += NWARP * 32)
+        coef_s[(i / (PD + 1)) * C::CS + i % (PD + 1)] = window_coef<T>(a.wp, i / (PD + 1), i % (PD + 1));
     __syncthreads();
 
     const int4 s_first = a.segs[wi.y];
@@ -115,20 +122,22 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
             for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;  // in [0, B)
             for (int qb = q0; qb < q1; qb += 32) {
                 const int cnt = min(32, q1 - qb);
-                if (lane < cnt) {
-                    const int q = qb + lane;
-                    const T vv = vr[a.perm[q]];
-                    T w[W2];
-#pragma unroll
-                    for (int k = 0; k < DW; ++k) {
-                        Weights<T, M>::eval(frac[(size_t)k * a.total + q], a.wp, w);
-                        if (k == DW - 1) {
-#pragma unroll
-                            for (int j = 0; j < W2; ++j) w[j] *= vv;
-                        }
-#pragma unroll
-                        for (int j = 0; j < W2; ++j) wts[lane * PS + k * WS + j] = w[j];
+                // the batch's weights, one (point, axis, pair of offsets) per lane and round: a
+                // batch of few points (sparse cells) still keeps the warp's lanes busy
+                for (int t = lane; t < cnt * DW * M; t += 32) {
+                    const int pl = t / (DW * M);
+                    const int rem = t - pl * (DW * M);
+                    const int k = rem / M, j = rem - k * M;
+                    const int q = qb + pl;
+                    T lo, hi;
+                    window_pair<T, PD>(frac[(size_t)k * a.total + q], coef_s + j * C::CS, lo, hi);
+                    if (k == DW - 1) {
+                        const T vv = vr[a.perm[q]];
+                        lo *= vv;
+                        hi *= vv;
                     }
+                    wts[pl * PS + k * WS + j] = lo;
+                    wts[pl * PS + k * WS + W2 - 1 - j] = hi;
                 }
                 __syncwarp();
 #pragma unroll

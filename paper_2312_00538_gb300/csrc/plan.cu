@@ -302,7 +302,7 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     p->prec = prec;
     p->interp_flags = flags & 6;
     p->wi_max = wi_max;
-    p->B = prec == ANOVA_FP64 ? 2 : 4;
+    p->B = prec == ANOVA_FP64 ? kBinF64 : 4;
     p->NB = p->n_os / p->B;
     p->tile_w = p->B + 2 * m - 1;
     p->stream = reinterpret_cast<cudaStream_t>(stream);
