@@ -205,15 +205,15 @@ __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, 
 // L(i, a) L(i, b) / theta_i, for 32 x 32 tiles of the lower triangle, FP64 accumulation.
 constexpr int kCoreRows = 2048;
 
-__global__ void __launch_bounds__(256) k_core_partial(const float *__restrict__ L, const double *__restrict__ theta,
-                                                      long long n, int r, const int2 *__restrict__ tiles,
+__global__ void __launch_bounds__(256) k_core_partial(const float *__restrict__ L, const double *__restrict__ itheta,
+                                                      long long n, int r, int chunk_rows, const int2 *__restrict__ tiles,
                                                       double *__restrict__ part) {
     __shared__ double A[32][33];
     __shared__ double Bm[32][33];
     const int2 t = tiles[blockIdx.x];
     const int a0 = t.x * 32, b0 = t.y * 32;
-    const long long i0 = (long long)blockIdx.y * kCoreRows;
-    const long long i1 = min(n, i0 + kCoreRows);
+    const long long i0 = (long long)blockIdx.y * chunk_rows;
+    const long long i1 = min(n, i0 + chunk_rows);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
     double acc[4] = {0, 0, 0, 0};
     for (long long ib = i0; ib < i1; ib += 32) {
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_core_partial(const float *__restrict__ 
             const long long i = ib + rr;
             double va = 0.0, vb = 0.0;
             if (i < i1) {
-                const double it = 1.0 / theta[i];
+                const double it = itheta[i];
                 if (a0 + cc < r) va = (double)L[(long long)(a0 + cc) * n + i] * it;
                 if (b0 + cc < r) vb = (double)L[(long long)(b0 + cc) * n + i];
             }
@@ -266,105 +266,120 @@ __global__ void k_core_sum(const double *__restrict__ part, int nchunks, int nti
     }
 }
 
-// In-place Cholesky of the SPD r x r matrix M (row-major, lower factor kept), one CTA.
-// Sets *info = 0 on success, k + 1 if the k-th pivot is not positive.
-__global__ void __launch_bounds__(1024) k_cholesky(double *M, int r, int *info) {
-    __shared__ double piv;
+// In-place Cholesky M = R R^T of the SPD r x r matrix M (row-major, lower factor R kept; the
+// strict upper triangle is left as it was), one CTA, right-looking: pivot, scale the column by the
+// pivot's reciprocal, then a warp per trailing row updates it. Sets *info = 0 on success, k + 1 if
+// the k-th pivot is not positive. idx maps (i, j <= i) to the storage of A.
+template <typename Idx>
+__device__ __forceinline__ void cholesky_cta(double *A, int r, int *bad_out, double *dinv, Idx idx) {
+    __shared__ double inv_piv;
     __shared__ int bad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (threadIdx.x == 0) {
-            const double dk = M[(long long)k * r + k];
+            const double dk = A[idx(k, k)];
             if (!(dk > 0.0)) bad = k + 1;
-            piv = sqrt(dk > 0.0 ? dk : 1.0);
-            M[(long long)k * r + k] = piv;
+            const double pv = sqrt(dk > 0.0 ? dk : 1.0);
+            A[idx(k, k)] = pv;
+            inv_piv = 1.0 / pv;
+            dinv[k] = inv_piv;
         }
         __syncthreads();
         if (bad) break;
-        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) M[(long long)i * r + k] /= piv;
+        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[idx(i, k)] *= inv_piv;
         __syncthreads();
-        const int m = r - k - 1;
-        for (long long e = threadIdx.x; e < (long long)m * m; e += blockDim.x) {
-            const int i = k + 1 + (int)(e / m), jj = k + 1 + (int)(e % m);
-            if (jj <= i) M[(long long)i * r + jj] -= M[(long long)i * r + k] * M[(long long)jj * r + k];
+        for (int i = k + 1 + warp; i < r; i += nwarps) {
+            const double lik = A[idx(i, k)];
+            for (int jj = k + 1 + lane; jj <= i; jj += 32) A[idx(i, jj)] -= lik * A[idx(jj, k)];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *info = bad;
+    if (threadIdx.x == 0) *bad_out = bad;
 }
 
-// Solve (R R^T) z = u for the lower Cholesky factor R (row-major): the CTA stages R's lower
-// triangle in shared memory (r <= kSmemCholMax; otherwise it is read from global memory), then
-// one warp runs the forward and backward substitutions with warp-level synchronisation only.
-__global__ void __launch_bounds__(256) k_chol_solve_warp(const double *__restrict__ R, int r, const double *__restrict__ u,
-                                                          double *__restrict__ z) {
-    extern __shared__ double sm[];
-    const bool in_smem = r <= 160;
-    double *zs = sm;
-    double *Rs = sm + r;
-    for (int i = threadIdx.x; i < r; i += blockDim.x) zs[i] = u[i];
-    if (in_smem)
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[e];
-    __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const double *A = in_smem ? Rs : R;
-    const int lane = threadIdx.x;
-    for (int k = 0; k < r; ++k) {  // R w = u
-        const double zk = zs[k] / A[(long long)k * r + k];
-        __syncwarp();
-        if (lane == 0) zs[k] = zk;
-        for (int i = k + 1 + lane; i < r; i += 32) zs[i] -= A[(long long)i * r + k] * zk;
-        __syncwarp();
-    }
-    for (int k = r - 1; k >= 0; --k) {  // R^T z = w
-        const double zk = zs[k] / A[(long long)k * r + k];
-        __syncwarp();
-        if (lane == 0) zs[k] = zk;
-        for (int i = lane; i < k; i += 32) zs[i] -= A[(long long)k * r + i] * zk;
-        __syncwarp();
-    }
-    for (int i = lane; i < r; i += 32) z[i] = zs[i];
+struct RowMajorIdx {
+    int r;
+    __device__ __forceinline__ long long operator()(int i, int j) const { return (long long)i * r + j; }
+};
+struct PackedIdx {
+    __device__ __forceinline__ int operator()(int i, int j) const { return i * (i + 1) / 2 + j; }
+};
+
+__global__ void __launch_bounds__(1024) k_cholesky(double *M, int r, int *info, double *dinv) {
+    cholesky_cta(M, r, info, dinv, RowMajorIdx{r});
 }
 
-// In-place Cholesky as k_cholesky, with the matrix staged in shared memory (r <= kSmemCholMax).
-constexpr int kSmemCholMax = 160;
+// The same with the lower triangle packed in shared memory (r(r + 1)/2 doubles, r <= kSmemCholMax).
+constexpr int kSmemCholMax = 240;
 
-__global__ void __launch_bounds__(1024) k_cholesky_smem(double *M, int r, int *info) {
+__global__ void __launch_bounds__(1024) k_cholesky_smem(double *M, int r, int *info, double *dinv) {
     extern __shared__ double A[];
-    __shared__ double piv;
-    __shared__ int bad;
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) A[e] = M[e];
-    if (threadIdx.x == 0) bad = 0;
+    for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
+        for (int j = threadIdx.x & 31; j <= i; j += 32) A[i * (i + 1) / 2 + j] = M[(long long)i * r + j];
     __syncthreads();
-    for (int k = 0; k < r; ++k) {
-        if (threadIdx.x == 0) {
-            const double dk = A[k * r + k];
-            if (!(dk > 0.0)) bad = k + 1;
-            piv = sqrt(dk > 0.0 ? dk : 1.0);
-            A[k * r + k] = piv;
-        }
-        __syncthreads();
-        if (bad) break;
-        for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) A[i * r + k] /= piv;
-        __syncthreads();
-        const int m = r - k - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            const int i = k + 1 + e / m, jj = k + 1 + e % m;
-            if (jj <= i) A[i * r + jj] -= A[i * r + k] * A[jj * r + k];
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) M[e] = A[e];
-    if (threadIdx.x == 0) *info = bad;
+    cholesky_cta(A, r, info, dinv, PackedIdx{});
+    __syncthreads();
+    for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
+        for (int j = threadIdx.x & 31; j <= i; j += 32) M[(long long)i * r + j] = A[i * (i + 1) / 2 + j];
 }
 
-// u_part[c](q) = sum_{i in chunk c} L(i, q) t_i with t = y .* g ./ theta. Grid: (row chunks,
-// groups of 8 columns); one warp per column, lanes over the chunk's rows.
+// W = R^{-1} for the lower Cholesky factor R (row-major; dinv = reciprocals of its diagonal):
+// one warp per column j runs the forward substitution R w = e_j (w_i = 0 for i < j); W is written
+// row-major (Wl, lower) and column-major (Wc), zeros above the diagonal. Then M^{-1} v = W^T (W v):
+// two parallel triangular products per application instead of two sequential substitutions. One
+// warp per CTA, so that the columns' FP64 work spreads over the SMs.
+__global__ void __launch_bounds__(32) k_tri_inv(const double *__restrict__ R, const double *__restrict__ dinv, int r,
+                                                double *__restrict__ Wl, double *__restrict__ Wc) {
+    extern __shared__ double w[];
+    const int lane = threadIdx.x;
+    const int j = blockIdx.x;
+    for (int i = j; i < r; ++i) {
+        double s = 0.0;
+        for (int k = j + lane; k < i; k += 32) s = fma(R[(long long)i * r + k], w[k], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double wi = ((i == j ? 1.0 : 0.0) - s) * dinv[i];
+        if (lane == 0) w[i] = wi;
+        __syncwarp();
+    }
+    for (int i = lane; i < r; i += 32) {
+        const double v = i >= j ? w[i] : 0.0;
+        Wl[(long long)i * r + j] = v;
+        Wc[(long long)j * r + i] = v;
+    }
+}
+
+// out[q] = sum over k of A[q r + k] x[k], k <= q (lower = 1) or k >= q (lower = 0); a warp per q.
+__global__ void __launch_bounds__(256) k_trmv(const double *__restrict__ A, int r, int lower,
+                                              const double *__restrict__ x, double *__restrict__ out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 8 + warp;
+    if (q >= r) return;
+    const int k0 = lower ? 0 : q, k1 = lower ? q + 1 : r;
+    double s = 0.0;
+    for (int k = k0 + lane; k < k1; k += 32) s = fma(A[(long long)q * r + k], x[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[q] = s;
+}
+
+__global__ void k_recip(const double *__restrict__ a, long long n, double *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = 1.0 / a[i];
+}
+
+// h = y .* g ./ theta (with the stored reciprocals)
+__global__ void k_scaled_rhs(const double *__restrict__ y, const double *__restrict__ g,
+                             const double *__restrict__ itheta, long long n, double *__restrict__ h) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        h[i] = y[i] * g[i] * itheta[i];
+}
+
+// u_part[c](q) = sum_{i in chunk c} L(i, q) h_i. Grid: (row chunks, groups of 8 columns); one
+// warp per column, lanes over the chunk's rows.
 constexpr int kApplyRows = 1024;
 
-__global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, const double *__restrict__ theta,
-                                                 const double *__restrict__ y, const double *__restrict__ g,
+__global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, const double *__restrict__ h,
                                                  long long n, int r, double *__restrict__ upart) {
     const long long i0 = (long long)blockIdx.x * kApplyRows;
     const long long i1 = min(n, i0 + kApplyRows);
@@ -373,7 +388,7 @@ __global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, co
     if (q >= r) return;
     const float *col = L + (long long)q * n;
     double s = 0.0;
-    for (long long i = i0 + lane; i < i1; i += 32) s += (double)col[i] * (y[i] * g[i] / theta[i]);
+    for (long long i = i0 + lane; i < i1; i += 32) s = fma((double)col[i], h[i], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) upart[(long long)blockIdx.x * r + q] = s;
 }
@@ -387,18 +402,30 @@ __global__ void k_panel_t_sum(const double *__restrict__ upart, int nchunks, int
 }
 
 // x_i = g_i / theta_i - (y_i / theta_i) sum_q L(i, q) z_q for i < n; x_n = g_n / s_schur.
-__global__ void __launch_bounds__(256) k_panel_n(const float *__restrict__ L, const double *__restrict__ theta,
+// 32 rows per CTA (one per lane); the 8 warps split the columns q and their partial sums are
+// added in a fixed order.
+__global__ void __launch_bounds__(256) k_panel_n(const float *__restrict__ L, const double *__restrict__ itheta,
                                                  const double *__restrict__ y, const double *__restrict__ g,
                                                  const double *__restrict__ z, long long n, int r,
                                                  double *__restrict__ x, const double *__restrict__ schur) {
-    extern __shared__ double zs[];
+    extern __shared__ double sm[];
+    double *zs = sm;
+    double *ps = sm + r;
     for (int q = threadIdx.x; q < r; q += blockDim.x) zs[q] = z[q];
     __syncthreads();
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < r; ++q) s += (double)L[(long long)q * n + i] * zs[q];
-        const double it = 1.0 / theta[i];
-        x[i] = g[i] * it - y[i] * it * s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long i = (long long)blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (i < n)
+        for (int q = warp; q < r; q += 8) s = fma((double)L[(long long)q * n + i], zs[q], s);
+    ps[warp * 32 + lane] = s;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += ps[w * 32 + lane];
+        const double it = itheta[i];
+        x[i] = g[i] * it - y[i] * it * t;
     }
     if (schur && blockIdx.x == 0 && threadIdx.x == 0) x[n] = g[n] / *schur;
 }
@@ -612,7 +639,7 @@ void lowrank_release(lowrank *lr) {
     if (!lr) return;
     void *bufs[] = {lr->L64, lr->L32, lr->d, lr->piv_dev, lr->dpiv, lr->stop, lr->partial, lr->M,
                     lr->u, lr->z, lr->upart, lr->tiles, lr->cpart, lr->info, lr->tmp,
-                    lr->dpart, lr->schur};
+                    lr->dpart, lr->schur, lr->Wl, lr->Wc, lr->tmp2, lr->dinv, lr->itheta, lr->hbuf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete lr;
@@ -759,7 +786,14 @@ static anova_status lowrank_finish(lowrank *lr) {
     for (int a = 0; a < nt; ++a)
         for (int b = 0; b <= a; ++b) tiles.push_back(make_int2(a, b));
     lr->ntiles = (int)tiles.size();
-    lr->nchunks = (int)((n + kCoreRows - 1) / kCoreRows);
+    {
+        // row chunks of the core's partial tiles: about 8 CTAs per SM over all tiles, at least
+        // 256 rows per chunk (multiples of 32)
+        const long long want = std::max<long long>(1, (152LL * 8 + lr->ntiles - 1) / lr->ntiles);
+        const long long chunks = std::max<long long>(1, std::min(want, (n + 255) / 256));
+        lr->core_rows = (int)(((n + chunks - 1) / chunks + 31) / 32 * 32);
+        lr->nchunks = (int)((n + lr->core_rows - 1) / lr->core_rows);
+    }
     lr->napply = (int)((n + kApplyRows - 1) / kApplyRows);
     if ((cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
         (cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
@@ -771,7 +805,13 @@ static anova_status lowrank_finish(lowrank *lr) {
         (cudaMalloc(&lr->info, sizeof(int))) != cudaSuccess ||
         (cudaMalloc(&lr->tmp, sizeof(double) * (n + 1))) != cudaSuccess ||
         (cudaMalloc(&lr->dpart, sizeof(double) * 1024)) != cudaSuccess ||
-        (cudaMalloc(&lr->schur, sizeof(double))) != cudaSuccess)
+        (cudaMalloc(&lr->schur, sizeof(double))) != cudaSuccess ||
+        (cudaMalloc(&lr->Wl, sizeof(double) * rank * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->Wc, sizeof(double) * rank * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->tmp2, sizeof(double) * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->dinv, sizeof(double) * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->itheta, sizeof(double) * n)) != cudaSuccess ||
+        (cudaMalloc(&lr->hbuf, sizeof(double) * n)) != cudaSuccess)
         return fail(ANOVA_ERR_OOM, "low-rank allocation failed");
     ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -904,21 +944,19 @@ static anova_status per_window_build(anova_plan *p, lowrank *lr, int r, double e
 // Woodbury apply of the (n x n) block: x[0:n] = A^{-1} g[0:n]; if with_schur, x[n] = g[n]/s.
 anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, const double *g, double *x,
                             bool with_schur) {
+    (void)theta;  // the reciprocals stored by set_theta (theta must be the array given there)
     anova_plan *p = lr->plan;
     cudaStream_t st = p->stream;
     const long long n = lr->n;
     const int r = lr->rank;
-    k_panel_t<<<dim3(lr->napply, (r + 7) / 8), 256, 0, st>>>(lr->L32, theta, y, g, n, r, lr->upart);
+    k_scaled_rhs<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(y, g, lr->itheta, n, lr->hbuf);
+    k_panel_t<<<dim3(lr->napply, (r + 7) / 8), 256, 0, st>>>(lr->L32, lr->hbuf, n, r, lr->upart);
     k_panel_t_sum<<<grid_for(r, 128), 128, 0, st>>>(lr->upart, lr->napply, r, lr->u);
-    {
-        const size_t shm = sizeof(double) * (r + (r <= 160 ? (size_t)r * r : 0));
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            k_chol_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * (160 + 160 * 160)));
-        if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute");
-        k_chol_solve_warp<<<1, 256, shm, st>>>(lr->M, r, lr->u, lr->z);   // z = M^{-1} u
-    }
-    k_panel_n<<<grid_for(n, 256, 152 * 8), 256, sizeof(double) * r, st>>>(lr->L32, theta, y, g, lr->z, n, r, x,
-                                                                          with_schur ? lr->schur : nullptr);
+    // z = M^{-1} u = W^T (W u)
+    k_trmv<<<(r + 7) / 8, 256, 0, st>>>(lr->Wl, r, 1, lr->u, lr->tmp2);
+    k_trmv<<<(r + 7) / 8, 256, 0, st>>>(lr->Wc, r, 0, lr->tmp2, lr->z);
+    k_panel_n<<<(unsigned)((n + 31) / 32), 256, sizeof(double) * (r + 256), st>>>(
+        lr->L32, lr->itheta, y, g, lr->z, n, r, x, with_schur ? lr->schur : nullptr);
     ANOVA_CUDA_TRY(cudaGetLastError());
     return ANOVA_OK;
 }
@@ -928,22 +966,26 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
     cudaStream_t st = p->stream;
     const long long n = lr->n;
     const int r = lr->rank;
-    k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, theta, n, r, (const int2 *)lr->tiles,
-                                                                   lr->cpart);
+    k_recip<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(theta, n, lr->itheta);
+    k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, lr->itheta, n, r, lr->core_rows,
+                                                                   (const int2 *)lr->tiles, lr->cpart);
     k_core_sum<<<lr->ntiles, 256, 0, st>>>(lr->cpart, lr->nchunks, lr->ntiles, (const int2 *)lr->tiles, r, lr->M);
     if (r <= kSmemCholMax) {
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * kSmemCholMax * kSmemCholMax));
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * kSmemCholMax * (kSmemCholMax + 1) / 2));
         if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute");
-        k_cholesky_smem<<<1, 1024, sizeof(double) * r * r, st>>>(lr->M, r, lr->info);
+        k_cholesky_smem<<<1, 1024, sizeof(double) * r * (r + 1) / 2, st>>>(lr->M, r, lr->info, lr->dinv);
     } else {
-        k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info);
+        k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info, lr->dinv);
     }
     ANOVA_CUDA_TRY(cudaGetLastError());
     int info = 0;
     ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
     if (info != 0) return fail(ANOVA_ERR_BREAKDOWN, "Woodbury core is not positive definite");
+    k_tri_inv<<<r, 32, sizeof(double) * r, st>>>(lr->M, lr->dinv, r, lr->Wl, lr->Wc);
+    ANOVA_CUDA_TRY(cudaGetLastError());
     // Schur complement s = y^T A^{-1} y of the block preconditioner
     anova_status s = woodbury_apply(lr, theta, y, y, lr->tmp, false);
     if (s != ANOVA_OK) return s;

@@ -19,6 +19,12 @@ struct lowrank {
     void *partial = nullptr;
     // Woodbury core
     double *M = nullptr;         // rank x rank, Cholesky factor after set_theta
+    double *Wl = nullptr, *Wc = nullptr;  // its inverse W (lower): row-major and column-major
+    double *itheta = nullptr;    // 1 / theta of the last set_theta (n)
+    double *hbuf = nullptr;      // y .* g ./ theta of the current apply (n)
+    double *tmp2 = nullptr;      // W u (rank)
+    double *dinv = nullptr;      // reciprocals of the Cholesky factor's diagonal (rank)
+    int core_rows = 0;           // rows per chunk of the core's partial Gram tiles
     double *u = nullptr, *upart = nullptr, *z = nullptr;
     void *tiles = nullptr;
     double *cpart = nullptr;
