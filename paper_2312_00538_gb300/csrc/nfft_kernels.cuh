@@ -112,70 +112,136 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
             const int mid = (lo + hi + 1) >> 1;
             if (a.segs[mid].y <= pw0) lo = mid; else hi = mid - 1;
         }
-        for (int s = lo; s < wi.z; ++s) {
-            const int4 sg = a.segs[s];
-            if (sg.y >= pw1) break;
-            const int q0 = max(sg.y, pw0), q1 = min(sg.y + sg.z, pw1);
-            if (q0 >= q1) continue;
-            int lc[3];
+        if constexpr (DW == 3) {
+            for (int s = lo; s < wi.z; ++s) {
+                const int4 sg = a.segs[s];
+                if (sg.y >= pw1) break;
+                const int q0 = max(sg.y, pw0), q1 = min(sg.y + sg.z, pw1);
+                if (q0 >= q1) continue;
+                int lc[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;  // in [0, B)
-            for (int qb = q0; qb < q1; qb += 32) {
-                const int cnt = min(32, q1 - qb);
-                // the batch's weights, one (point, axis, pair of offsets) per lane and round: a
-                // batch of few points (sparse cells) still keeps the warp's lanes busy
-                for (int t = lane; t < cnt * DW * M; t += 32) {
-                    const int pl = t / (DW * M);
-                    const int rem = t - pl * (DW * M);
-                    const int k = rem / M, j = rem - k * M;
-                    const int q = qb + pl;
-                    T lo, hi;
-                    window_pair<T, PD>(frac[(size_t)k * a.total + q], coef_s + j * C::CS, lo, hi);
-                    if (k == DW - 1) {
-                        const T vv = vr[a.perm[q]];
-                        lo *= vv;
-                        hi *= vv;
+                for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;  // in [0, B)
+                for (int qb = q0; qb < q1; qb += 32) {
+                    const int cnt = min(32, q1 - qb);
+                    // the batch's weights, one (point, axis, pair of offsets) per lane and round: a
+                    // batch of few points (sparse cells) still keeps the warp's lanes busy
+                    for (int t = lane; t < cnt * DW * M; t += 32) {
+                        const int pl = t / (DW * M);
+                        const int rem = t - pl * (DW * M);
+                        const int k = rem / M, j = rem - k * M;
+                        const int q = qb + pl;
+                        T lo, hi;
+                        window_pair<T, PD>(frac[(size_t)k * a.total + q], coef_s + j * C::CS, lo, hi);
+                        if (k == DW - 1) {
+                            const T vv = vr[a.perm[q]];
+                            lo *= vv;
+                            hi *= vv;
+                        }
+                        wts[pl * PS + k * WS + j] = lo;
+                        wts[pl * PS + k * WS + W2 - 1 - j] = hi;
                     }
-                    wts[pl * PS + k * WS + j] = lo;
-                    wts[pl * PS + k * WS + W2 - 1 - j] = hi;
-                }
-                __syncwarp();
+                    __syncwarp();
 #pragma unroll
-                for (int t0 = 0; t0 < RPL; t0 += RCH) {
-                    T acc[RCH][W2];
+                    for (int t0 = 0; t0 < RPL; t0 += RCH) {
+                        T acc[RCH][W2];
 #pragma unroll
-                    for (int tt = 0; tt < RCH; ++tt)
+                        for (int tt = 0; tt < RCH; ++tt)
 #pragma unroll
-                        for (int c = 0; c < W2; ++c) acc[tt][c] = T(0);
-                    for (int j = 0; j < cnt; ++j) {
-                        const T *pw = wts + j * PS;
-                        T wz[W2];
-                        lds_vec<T, W2>(pw + (DW - 1) * WS, wz);
+                            for (int c = 0; c < W2; ++c) acc[tt][c] = T(0);
+                        for (int j = 0; j < cnt; ++j) {
+                            const T *pw = wts + j * PS;
+                            T wz[W2];
+                            lds_vec<T, W2>(pw + (DW - 1) * WS, wz);
+#pragma unroll
+                            for (int tt = 0; tt < RCH; ++tt) {
+                                const int t = t0 + tt;
+                                if (t < RPL) {
+                                    T rw;
+                                    if (DW == 3) rw = pw[ra[t]] * pw[WS + rb[t]];
+                                    else if (DW == 2) rw = pw[ra[t]];
+                                    else rw = T(1);
+#pragma unroll
+                                    for (int c = 0; c < W2; ++c) acc[tt][c] = fma(rw, wz[c], acc[tt][c]);
+                                }
+                            }
+                        }
 #pragma unroll
                         for (int tt = 0; tt < RCH; ++tt) {
                             const int t = t0 + tt;
-                            if (t < RPL) {
-                                T rw;
-                                if (DW == 3) rw = pw[ra[t]] * pw[WS + rb[t]];
-                                else if (DW == 2) rw = pw[ra[t]];
-                                else rw = T(1);
+                            if (t < RPL && rvalid[t]) {
+                                int base;
+                                if (DW == 3) base = ((lc[0] + ra[t]) * TW + (lc[1] + rb[t])) * TW + lc[2];
+                                else if (DW == 2) base = (lc[0] + ra[t]) * TW + lc[1];
+                                else base = lc[0];
 #pragma unroll
-                                for (int c = 0; c < W2; ++c) acc[tt][c] = fma(rw, wz[c], acc[tt][c]);
+                                for (int c = 0; c < W2; ++c) tile[base + c] += acc[tt][c];
                             }
                         }
                     }
+                    __syncwarp();
+                }
+            }
+        } else {
+            // 1-D and 2-D footprints: a lane owns one footprint row (2-D: row a, 1-D: the single
+            // row) for every PPS-th point of the batch; the PPS point slots keep their sums over
+            // the cell's batches and are folded in a fixed order when the cell ends
+            constexpr int LR = DW == 2 ? W2 : 1;  // lanes per point
+            constexpr int PPS = 32 / LR;          // point slots per warp
+            const int slot = lane / LR, row = lane % LR;
+            const bool lane_ok = slot < PPS;
+            for (int s = lo; s < wi.z; ++s) {
+                const int4 sg = a.segs[s];
+                if (sg.y >= pw1) break;
+                const int q0 = max(sg.y, pw0), q1 = min(sg.y + sg.z, pw1);
+                if (q0 >= q1) continue;
+                int lc[3];
 #pragma unroll
-                    for (int tt = 0; tt < RCH; ++tt) {
-                        const int t = t0 + tt;
-                        if (t < RPL && rvalid[t]) {
-                            int base;
-                            if (DW == 3) base = ((lc[0] + ra[t]) * TW + (lc[1] + rb[t])) * TW + lc[2];
-                            else if (DW == 2) base = (lc[0] + ra[t]) * TW + lc[1];
-                            else base = lc[0];
+                for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;  // in [0, B)
+                T acc[W2];
 #pragma unroll
-                            for (int c = 0; c < W2; ++c) tile[base + c] += acc[tt][c];
+                for (int c = 0; c < W2; ++c) acc[c] = T(0);
+                for (int qb = q0; qb < q1; qb += 32) {
+                    const int cnt = min(32, q1 - qb);
+                    for (int t = lane; t < cnt * DW * M; t += 32) {
+                        const int pl = t / (DW * M);
+                        const int rem = t - pl * (DW * M);
+                        const int k = rem / M, j = rem - k * M;
+                        const int q = qb + pl;
+                        T lo_w, hi_w;
+                        window_pair<T, PD>(frac[(size_t)k * a.total + q], coef_s + j * C::CS, lo_w, hi_w);
+                        if (k == DW - 1) {
+                            const T vv = vr[a.perm[q]];
+                            lo_w *= vv;
+                            hi_w *= vv;
                         }
+                        wts[pl * PS + k * WS + j] = lo_w;
+                        wts[pl * PS + k * WS + W2 - 1 - j] = hi_w;
                     }
+                    __syncwarp();
+                    if (lane_ok)
+                        for (int jp = slot; jp < cnt; jp += PPS) {
+                            const T *pw = wts + jp * PS;
+                            const T rw = DW == 2 ? pw[row] : T(1);
+                            T wz[W2];
+                            lds_vec<T, W2>(pw + (DW - 1) * WS, wz);
+#pragma unroll
+                            for (int c = 0; c < W2; ++c) acc[c] = fma(rw, wz[c], acc[c]);
+                        }
+                    __syncwarp();
+                }
+                // tree fold of the slots into slot 0 (lanes past the slots hold zeros)
+#pragma unroll
+                for (int k = 1; k < PPS; k <<= 1) {
+#pragma unroll
+                    for (int c = 0; c < W2; ++c) {
+                        const T other = __shfl_down_sync(0xffffffffu, acc[c], k * LR);
+                        if (lane_ok && slot % (2 * k) == 0 && slot + k < PPS) acc[c] += other;
+                    }
+                }
+                if (slot == 0) {
+                    const int base = DW == 2 ? (lc[0] + row) * TW + lc[1] : lc[0];
+#pragma unroll
+                    for (int c = 0; c < W2; ++c) tile[base + c] += acc[c];
                 }
                 __syncwarp();
             }
