@@ -997,7 +997,24 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             return (primal - dual) / std::max(1.0, std::fabs(primal)) <= tol && xa <= tol;
         };
         std::vector<double> hstep(kRedBlocks);
+        // f = K (y .* alpha) is updated as f += step K (y .* d_alpha) when the last FP64 residual
+        // of the Newton solve was taken at the final direction (that product is then at hand),
+        // and recomputed in full every kFullKya steps and before convergence is accepted
+        constexpr int kFullKya = 8;
+        bool f_incremental = false;
+        auto refresh = [&]() -> anova_status {
+            anova_status r;
+            if ((r = S.kya(dal, df)) != ANOVA_OK) return r;
+            if ((r = objectives(sums)) != ANOVA_OK) return r;
+            dual = sums[0] - 0.5 * sums[1];
+            primal = 0.5 * sums[1] + C * sums[2];
+            xa = std::fabs(sums[3]) / nxa0;
+            xl = std::sqrt(sums[4]) / nxl0;
+            f_incremental = false;
+            return ANOVA_OK;
+        };
         while (it < o.max_iter) {
+            if (done() && f_incremental && (s = refresh()) != ANOVA_OK) return s;
             if (done()) {
                 converged = true;
                 break;
@@ -1018,6 +1035,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             const double inner_tol = std::max(o.krylov_tol, 1e-6);
             double rel_prev = 1.0;
             bool solved = false;
+            bool kdelta_ready = false;  // S.k64 = K (y .* d_alpha) for the final direction
             for (int k = 0; k < o.refine_max; ++k) {
                 int iters = 0;
                 if (o.krylov == SVM_KRYLOV_GMRES) {
@@ -1034,6 +1052,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                 const double rel = std::sqrt(rn2) / gnorm;
                 if (rel <= o.krylov_tol) {
                     solved = true;
+                    kdelta_ready = true;
                     break;
                 }
                 if (rel > 0.5 * rel_prev) break;  // the FP32 operator no longer reduces the residual
@@ -1064,7 +1083,14 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             s_prev = step;
             k_axpy<<<nb, 256, 0, st>>>(step, ddelta, n, dal);
             lam += step * dlam;
-            if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
+            if (kdelta_ready && (it + 1) % kFullKya != 0) {
+                k_axpy<<<nb, 256, 0, st>>>(step, S.k64, n, df);
+                ANOVA_CUDA_TRY(cudaGetLastError());
+                f_incremental = true;
+            } else {
+                if ((s = S.kya(dal, df)) != ANOVA_OK) return s;
+                f_incremental = false;
+            }
             ++it;
             if ((s = objectives(sums)) != ANOVA_OK) return s;
             dual = sums[0] - 0.5 * sums[1];
@@ -1074,6 +1100,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
             if (!std::isfinite(dual) || !std::isfinite(primal))
                 return fail(ANOVA_ERR_NONFINITE, "interior point iterate is not finite");
         }
+        if (!converged && f_incremental && (s = refresh()) != ANOVA_OK) return s;
         if (!converged && done()) converged = true;
         ANOVA_CUDA_TRY(cudaMemcpyAsync(alpha_out, dal, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
