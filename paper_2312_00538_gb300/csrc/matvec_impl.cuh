@@ -26,9 +26,6 @@ constexpr int kAuxStreams = 3;           // concurrent window chains of one matv
 // FP32 3-D interpolation with m = 4: 2 = tensor cores where chosen, 0 = always one point per lane
 #define ANOVA_INTERP_VARIANT 2
 #endif
-#ifndef ANOVA_SPREAD_RB
-#define ANOVA_SPREAD_RB 1  // right-hand sides per CTA of the packed FP32 spread (1, 2, 4)
-#endif
 #ifndef ANOVA_SPREAD_LPP
 #define ANOVA_SPREAD_LPP 32  // lanes per point in the packed FP32 spread (16 or 32)
 #endif
@@ -106,28 +103,16 @@ cudaError_t resident_ctas(K kern, int threads, size_t smem, int cap, int *out) {
     return cudaSuccess;
 }
 
-template <int M, int LPP, int RB>
-cudaError_t launch_spread3_x2_rb(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
-    constexpr int B = Prec<float>::B;
-    // several right-hand sides per CTA need one warp tile each: fewer warps keep 3 CTAs per SM
-    constexpr int NW = RB == 1 ? Prec<float>::SPREAD_WARPS : (RB == 2 ? 4 : 2);
-    using C = SpreadX2Cfg<M, B, NW, LPP, RB>;
-    auto kern = k_spread3_x2<M, B, NW, LPP, RB>;
+template <int M, int LPP>
+cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
+    constexpr int B = Prec<float>::B, NW = Prec<float>::SPREAD_WARPS;
+    using C = SpreadX2Cfg<M, B, NW, LPP>;
+    auto kern = k_spread3_x2<M, B, NW, LPP>;
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(nblocks, (nrhs + RB - 1) / RB), NW * 32, C::smem, st>>>(a);
+    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
     return cudaGetLastError();
-}
-
-template <int M, int LPP>
-cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
-    // right-hand sides per CTA share the weights (ANOVA_SPREAD_RB: the most per CTA)
-    if constexpr (ANOVA_SPREAD_RB >= 4)
-        if (nrhs >= 4) return launch_spread3_x2_rb<M, LPP, 4>(a, nblocks, nrhs, st);
-    if constexpr (ANOVA_SPREAD_RB >= 2)
-        if (nrhs >= 2) return launch_spread3_x2_rb<M, LPP, 2>(a, nblocks, nrhs, st);
-    return launch_spread3_x2_rb<M, LPP, 1>(a, nblocks, nrhs, st);
 }
 
 template <int M>

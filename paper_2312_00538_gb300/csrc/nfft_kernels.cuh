@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
 // points per step with fma.rn.f32x2. The staged weights are laid out so that every load is a
 // 64- or 128-bit broadcast: X duplicated into pairs and permuted so that a lane's rows are
 // contiguous, Y duplicated into pairs, Z (times v) plain.
-template <int M, int B, int NWARP, int LPP = 16, int RB = 1>
+template <int M, int B, int NWARP, int LPP = 16>
 struct SpreadX2Cfg {
     static constexpr int W2 = 2 * M;
     static constexpr int RPL = W2 * W2 / LPP;        // rows per lane (LPP lanes share a point)
@@ -272,19 +272,15 @@ struct SpreadX2Cfg {
     static constexpr int TW = B + W2 - 1;
     static constexpr int TV = TW * TW * TW;
     static constexpr int TVP = (TV + 3) / 4 * 4;
-    // staged floats per point: X, Y, and Z times v of each of the RB right-hand sides
-    static constexpr int XO = 0, YO = W2, ZO = 2 * W2, PS = (2 + RB) * W2;
+    static constexpr int XO = 0, YO = W2, ZO = 2 * W2, PS = 3 * W2;      // staged floats per point
     static constexpr int SEG_CACHE = 128;                               // segments kept in shared memory
-    // warp tiles (one per right-hand side), staged weights, the item's segments
-    static constexpr size_t smem =
-        sizeof(float) * ((size_t)NWARP * RB * TVP + (size_t)NWARP * 32 * PS) + 16 * SEG_CACHE;
+    // warp tiles, staged weights, the item's segments
+    static constexpr size_t smem = sizeof(float) * ((size_t)NWARP * TVP + (size_t)NWARP * 32 * PS) + 16 * SEG_CACHE;
 };
 
-// RB right-hand sides per CTA share the staged X and Y weights, the row products and the
-// coordinate loads; each keeps its own accumulators and warp tile.
-template <int M, int B, int NWARP, int LPP, int RB>
+template <int M, int B, int NWARP, int LPP>
 __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(SpreadArgs a) {
-    using C = SpreadX2Cfg<M, B, NWARP, LPP, RB>;
+    using C = SpreadX2Cfg<M, B, NWARP, LPP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
     constexpr int PPS = 32 / LPP;  // points per warp step
     constexpr int SPREAD_UNROLL = ANOVA_SPREAD_UNROLL / PPS > 0 ? ANOVA_SPREAD_UNROLL / PPS : 1;
@@ -293,18 +289,17 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
     static_assert(W2 % 4 == 0, "vector staging layout");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tiles_s = reinterpret_cast<float *>(smem_raw);
-    float *wts_s = tiles_s + NWARP * RB * C::TVP;
+    float *wts_s = tiles_s + NWARP * C::TVP;
 
     if (a.wi_begin + (int)blockIdx.x >= a.wi_end) return;
     const int wi_idx = a.order ? a.order[a.wi_begin + blockIdx.x] : a.wi_begin + blockIdx.x;
-    const int r0 = blockIdx.y * RB;              // first right-hand side of this CTA
-    const int nr = min(RB, a.nrhs - r0);         // right-hand sides present (the rest add zeros)
+    const int r = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = lane / LPP, lh = lane % LPP;
     const int4 wi = a.wis[wi_idx];
     const int bin[3] = {cell_coord(wi.w, 0), cell_coord(wi.w, 1), cell_coord(wi.w, 2)};
 
-    for (int i = threadIdx.x; i < NWARP * RB * C::TVP; i += NWARP * 32) tiles_s[i] = 0.0f;
+    for (int i = threadIdx.x; i < NWARP * C::TVP; i += NWARP * 32) tiles_s[i] = 0.0f;
     // the item's segments in shared memory (each warp searches them for its first point and
     // walks them in order)
     int4 *segs_s = reinterpret_cast<int4 *>(wts_s + NWARP * 32 * PS);
@@ -327,14 +322,9 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
     const float *fr1 = fr0 + a.total, *fr2 = fr0 + 2 * a.total;
     // v is read through the permutation: the permutation streams in sorted order and v (4 bytes
     // per point) stays in L2, so no sorted copy of v is written first
-    const float *vr = reinterpret_cast<const float *>(a.v) + (size_t)r0 * a.n;
-    // v of right-hand side rr at sorted position q (zero for right-hand sides past nrhs)
-    auto vsorted_at = [&](int q, float (&out)[RB]) {
-        const int pi = a.perm[q];
-#pragma unroll
-        for (int rr = 0; rr < RB; ++rr) out[rr] = rr < nr ? vr[(size_t)rr * a.n + pi] : 0.0f;
-    };
-    float *tile = tiles_s + warp * RB * C::TVP;  // tile of right-hand side rr at + rr * TVP
+    const float *vr = reinterpret_cast<const float *>(a.v) + (size_t)r * a.n;
+    auto vsorted_at = [&](int q) { return vr[a.perm[q]]; };
+    float *tile = tiles_s + warp * C::TVP;
     float *wts = wts_s + warp * 32 * PS;
     const int g = lh / W2;           // this lane's rows: a = g + S k, b = lh % W2
     const int rb = lh % W2;
@@ -355,22 +345,18 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
         int send = min(sg.y + sg.z, pw1);
         int cnt = min(32, send - q);
         // per-point inputs of the current batch (prefetched one batch ahead)
-        float fx = 0.f, fy = 0.f, fz = 0.f, vv[RB];
-#pragma unroll
-        for (int rr = 0; rr < RB; ++rr) vv[rr] = 0.f;
+        float fx = 0.f, fy = 0.f, fz = 0.f, vv = 0.f;
         if (lane < cnt) {
             fx = fr0[q + lane];
             fy = fr1[q + lane];
             fz = fr2[q + lane];
-            vsorted_at(q + lane, vv);
+            vv = vsorted_at(q + lane);
         }
-        f32x2 acc[RB][RPL][W2 / 2];
+        f32x2 acc[RPL][W2 / 2];
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr)
+        for (int k = 0; k < RPL; ++k)
 #pragma unroll
-            for (int k = 0; k < RPL; ++k)
-#pragma unroll
-                for (int c = 0; c < W2 / 2; ++c) acc[rr][k][c] = zero2();
+            for (int c = 0; c < W2 / 2; ++c) acc[k][c] = zero2();
         while (true) {
             // next batch: same piece, or the first batch of the next segment in range
             const int qn = q + cnt;
@@ -388,14 +374,12 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
                 }
             }
             const int cntn = done ? 0 : min(32, sendn - qn);
-            float nfx = 0.f, nfy = 0.f, nfz = 0.f, nvv[RB];
-#pragma unroll
-            for (int rr = 0; rr < RB; ++rr) nvv[rr] = 0.f;
+            float nfx = 0.f, nfy = 0.f, nfz = 0.f, nvv = 0.f;
             if (lane < cntn) {
                 nfx = fr0[qn + lane];
                 nfy = fr1[qn + lane];
                 nfz = fr2[qn + lane];
-                vsorted_at(qn + lane, nvv);
+                nvv = vsorted_at(qn + lane);
             }
             int4 sg_next2 = sg_next;
             if (newpiece && !done && sn + 1 < wi.z) sg_next2 = seg_at(sn + 1);
@@ -405,6 +389,9 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
                 Weights<float, M>::eval(fx, a.wp, wx);
                 Weights<float, M>::eval(fy, a.wp, wy);
                 Weights<float, M>::eval(fz, a.wp, wz);
+                const float vl = lane < cnt ? vv : 0.0f;
+#pragma unroll
+                for (int j = 0; j < W2; ++j) wz[j] *= vl;
                 float4 *dst = reinterpret_cast<float4 *>(wts + lane * PS);
                 // X at permuted positions a -> (a % S) * RPL + a / S, so a lane's rows are adjacent
 #pragma unroll
@@ -417,13 +404,7 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
 #pragma unroll
                 for (int b = 0; b < W2; b += 4) dst[(C::YO + b) / 4] = make_float4(wy[b], wy[b + 1], wy[b + 2], wy[b + 3]);
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    const float vl = lane < cnt ? vv[rr] : 0.0f;
-#pragma unroll
-                    for (int c = 0; c < W2; c += 4)
-                        dst[(C::ZO + rr * W2 + c) / 4] =
-                            make_float4(wz[c] * vl, wz[c + 1] * vl, wz[c + 2] * vl, wz[c + 3] * vl);
-                }
+                for (int c = 0; c < W2; c += 4) dst[(C::ZO + c) / 4] = make_float4(wz[c], wz[c + 1], wz[c + 2], wz[c + 3]);
             }
             __syncwarp();
             // steps in groups of SPREAD_UNROLL: lanes past the batch staged zero Z weights, so
@@ -435,7 +416,7 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
                 const int jj = j0 + ju;
                 const float *pw = wts + (PPS * jj + half) * PS;
                 float xr[RPL];
-                f32x2 z2[RB][W2 / 2];
+                f32x2 z2[W2 / 2];
                 const float yb = pw[C::YO + rb];
                 if constexpr (RPL % 4 == 0) {
 #pragma unroll
@@ -455,18 +436,13 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
                     for (int k = 0; k < RPL; ++k) xr[k] = pw[C::XO + g * RPL + k];
                 }
 #pragma unroll
-                for (int rr = 0; rr < RB; ++rr)
-#pragma unroll
-                    for (int c = 0; c < W2 / 2; c += 2)
-                        lds_pairs(pw + C::ZO + rr * W2 + 2 * c, z2[rr][c], z2[rr][c + 1]);
+                for (int c = 0; c < W2 / 2; c += 2) lds_pairs(pw + C::ZO + 2 * c, z2[c], z2[c + 1]);
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) {
                     const float rs = xr[k] * yb;
                     const f32x2 rw = make_float2(rs, rs);
 #pragma unroll
-                    for (int rr = 0; rr < RB; ++rr)
-#pragma unroll
-                        for (int c = 0; c < W2 / 2; ++c) acc[rr][k][c] = fma2(rw, z2[rr][c], acc[rr][k][c]);
+                    for (int c = 0; c < W2 / 2; ++c) acc[k][c] = fma2(rw, z2[c], acc[k][c]);
                 }
             }
             __syncwarp();
@@ -476,36 +452,33 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
                 int lc[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) lc[k] = cell_coord(sg.x, k) - bin[k] * B;
-#pragma unroll
-                for (int rr = 0; rr < RB; ++rr) {
-                    if constexpr (PPS == 2) {
-#pragma unroll
-                        for (int k = 0; k < RPL; ++k)
-#pragma unroll
-                            for (int c = 0; c < W2 / 2; ++c) {
-                                f32x2 o;
-                                o.x = __shfl_down_sync(0xffffffffu, acc[rr][k][c].x, 16);
-                                o.y = __shfl_down_sync(0xffffffffu, acc[rr][k][c].y, 16);
-                                acc[rr][k][c] = add2(acc[rr][k][c], o);
-                            }
-                    }
-                    if (half == 0) {
-#pragma unroll
-                        for (int k = 0; k < RPL; ++k) {
-                            const int ra = g + S * k;
-                            float *dst = tile + rr * C::TVP + ((lc[0] + ra) * TW + (lc[1] + rb)) * TW + lc[2];
-#pragma unroll
-                            for (int c = 0; c < W2 / 2; ++c) {
-                                dst[2 * c] += acc[rr][k][c].x;
-                                dst[2 * c + 1] += acc[rr][k][c].y;
-                            }
-                        }
-                    }
+                if constexpr (PPS == 2) {
 #pragma unroll
                     for (int k = 0; k < RPL; ++k)
 #pragma unroll
-                        for (int c = 0; c < W2 / 2; ++c) acc[rr][k][c] = zero2();
+                        for (int c = 0; c < W2 / 2; ++c) {
+                            f32x2 o;
+                            o.x = __shfl_down_sync(0xffffffffu, acc[k][c].x, 16);
+                            o.y = __shfl_down_sync(0xffffffffu, acc[k][c].y, 16);
+                            acc[k][c] = add2(acc[k][c], o);
+                        }
                 }
+                if (half == 0) {
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int ra = g + S * k;
+                        float *dst = tile + ((lc[0] + ra) * TW + (lc[1] + rb)) * TW + lc[2];
+#pragma unroll
+                        for (int c = 0; c < W2 / 2; ++c) {
+                            dst[2 * c] += acc[k][c].x;
+                            dst[2 * c + 1] += acc[k][c].y;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < RPL; ++k)
+#pragma unroll
+                    for (int c = 0; c < W2 / 2; ++c) acc[k][c] = zero2();
                 __syncwarp();
             }
             if (done) break;
@@ -520,19 +493,16 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
             fx = nfx;
             fy = nfy;
             fz = nfz;
-#pragma unroll
-            for (int rr = 0; rr < RB; ++rr) vv[rr] = nvv[rr];
+            vv = nvv;
         }
     }
     __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
-        float *out = reinterpret_cast<float *>(a.tiles) + ((size_t)wi_idx * a.nrhs + r0 + rr) * C::TV;
-        for (int i = threadIdx.x; i < C::TV; i += NWARP * 32) {
-            float s2 = 0.0f;
+    float *out = reinterpret_cast<float *>(a.tiles) + ((size_t)wi_idx * a.nrhs + r) * C::TV;
+    for (int i = threadIdx.x; i < C::TV; i += NWARP * 32) {
+        float s2 = 0.0f;
 #pragma unroll
-            for (int w = 0; w < NWARP; ++w) s2 += tiles_s[(w * RB + rr) * C::TVP + i];
-            out[i] = s2;
-        }
+        for (int w = 0; w < NWARP; ++w) s2 += tiles_s[w * C::TVP + i];
+        out[i] = s2;
     }
 }
 

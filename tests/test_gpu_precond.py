@@ -192,3 +192,29 @@ def test_randomised_nystrom_full_rank_and_fp32_plan(env):
     p32 = ab.anova_nfft_plan(X, W, 0.05, N=32, m=4, flags=ab.ANOVA_FP32)
     with pytest.raises(ab.AnovaError):
         ab.lowrank_precond_build(p32, ab.NYSTROM_RANDOM, 10, 0.0, seed=3)
+
+
+@pytest.mark.parametrize("rank", [240, 300])
+def test_woodbury_at_large_rank(env, rank):
+    """The core factor in packed shared memory (rank 240, the largest that fits) and in global
+    memory (rank 300), with its triangular inverse, against the dense oracle."""
+    torch, ab = env
+    n = 700
+    X, W, plan, K, rng = _setup(ab, n=n, ell=0.05, seed=9)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, rank, 0.0)
+    L, _ = _factor(torch, ab, lr, n)
+    assert L.shape[1] == rank
+    L32 = L.astype(np.float32).astype(np.float64)
+    y = np.where(rng.standard_normal(n) >= 0, 1.0, -1.0)
+    theta = np.exp(rng.uniform(-3, 3, n))
+    g = rng.standard_normal(n + 1)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    th, yy, gg = dev(theta), dev(y), dev(g)
+    x = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+    ab.lowrank_precond_set_theta(lr, th, yy)
+    ab.lowrank_precond_apply(lr, th, yy, gg, x)
+    torch.cuda.synchronize()
+    s = y @ op.woodbury_apply(L32, theta, y, y)
+    ref = op.blockdiag_apply(L32, theta, y, g, s)
+    got = x.cpu().numpy()
+    assert np.allclose(got, ref, rtol=1e-8, atol=1e-10 * np.max(np.abs(ref)))
