@@ -506,9 +506,12 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                 WindowInfo &wi = p->win[w];
                 wi.tile_begin[pass] = (int)ftiles.size();
                 int plo = 0, phi = 1, qlo = 0, qhi = 1;
+                // a pass transforms full lines along its axis for the box of the other axes: the
+                // input is zero outside the box on axes not yet transformed, and only the box is
+                // read on axes already transformed (by the later passes and the interpolation)
                 if (g.dw == 3) {
                     if (pass == 0) { plo = wi.box_lo[1]; phi = wi.box_hi[1]; qlo = wi.box_lo[2]; qhi = wi.box_hi[2]; }
-                    if (pass == 1) { plo = 0; phi = nos; qlo = wi.box_lo[2]; qhi = wi.box_hi[2]; }
+                    if (pass == 1) { plo = wi.box_lo[0]; phi = wi.box_hi[0]; qlo = wi.box_lo[2]; qhi = wi.box_hi[2]; }
                     if (pass == 2) { plo = wi.box_lo[0]; phi = wi.box_hi[0]; qlo = wi.box_lo[1]; qhi = wi.box_hi[1]; }
                 } else if (g.dw == 2) {
                     if (pass == 0) { qlo = wi.box_lo[1]; qhi = wi.box_hi[1]; }
