@@ -53,20 +53,23 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
                 }
             }
         } else {
+            // both halves in one instruction stream: t = partner + s * own (s = +1 above, -1
+            // below: a + b and a - b), then t * w with w = 1 above; at span 1 every twiddle is 1
             const bool top = (lane & h) == 0;
+            const T sg = top ? T(1) : T(-1);
             const int k = ((lane & ~h) & (2 * h - 1)) * (NOS / (2 * h));
-            const T wr = twr[k], wi = twi[k];
+            const T wr = top ? T(1) : twr[k], wi = top ? T(0) : twi[k];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 const T yr = __shfl_xor_sync(0xffffffffu, re[v], h);
                 const T yi = __shfl_xor_sync(0xffffffffu, im[v], h);
-                if (top) {
-                    re[v] += yr;
-                    im[v] += yi;
+                const T tr = fma(sg, re[v], yr), ti = fma(sg, im[v], yi);
+                if (h == 1) {
+                    re[v] = tr;
+                    im[v] = ti;
                 } else {
-                    const T dr = yr - re[v], di = yi - im[v];
-                    re[v] = dr * wr - di * wi;
-                    im[v] = dr * wi + di * wr;
+                    re[v] = tr * wr - ti * wi;
+                    im[v] = tr * wi + ti * wr;
                 }
             }
         }
@@ -82,25 +85,22 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
 #pragma unroll
     for (int h = 1; h <= NOS / 2; h <<= 1) {
         if (h < 32) {
+            // b * conj(w) below (w = 1 above, and everywhere at span 1), then partner + s * own
             const bool top = (lane & h) == 0;
+            const T sg = top ? T(1) : T(-1);
             const int k = ((lane & ~h) & (2 * h - 1)) * (NOS / (2 * h));
-            const T wr = twr[k], wi = twi[k];
+            const T wr = top ? T(1) : twr[k], wi = top ? T(0) : twi[k];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                if (!top) {  // b * conj(w)
+                if (h != 1) {
                     const T br = re[v], bi = im[v];
                     re[v] = br * wr + bi * wi;
                     im[v] = bi * wr - br * wi;
                 }
                 const T yr = __shfl_xor_sync(0xffffffffu, re[v], h);
                 const T yi = __shfl_xor_sync(0xffffffffu, im[v], h);
-                if (top) {
-                    re[v] += yr;
-                    im[v] += yi;
-                } else {
-                    re[v] = yr - re[v];
-                    im[v] = yi - im[v];
-                }
+                re[v] = fma(sg, re[v], yr);
+                im[v] = fma(sg, im[v], yi);
             }
         } else {
             const int hv = h / 32;
