@@ -29,6 +29,11 @@ struct ConvArgs {
     int zero_offset;         // 1: in/out are one window's grids (ignore the grid offset)
 };
 
+__device__ __forceinline__ float flip_sign(float x) { return __int_as_float(__float_as_int(x) ^ 0x80000000); }
+__device__ __forceinline__ double flip_sign(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 template <typename T, int NOS>
 __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], const T *twr,
                                           const T *twi, const T *d1, int lane) {
@@ -67,6 +72,11 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
                 if (h == 1) {
                     re[v] = tr;
                     im[v] = ti;
+                } else if (h == 2) {
+                    // w is 1 or -i: t * (-i) = ti - i tr, by selection and a sign flip
+                    const bool rot = !top && (lane & 1);
+                    re[v] = rot ? ti : tr;
+                    im[v] = rot ? flip_sign(tr) : ti;
                 } else {
                     re[v] = tr * wr - ti * wi;
                     im[v] = tr * wi + ti * wr;
@@ -92,7 +102,13 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
             const T wr = top ? T(1) : twr[k], wi = top ? T(0) : twi[k];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                if (h != 1) {
+                if (h == 2) {
+                    // conj(w) is 1 or +i: b * i = -bi + i br
+                    const bool rot = !top && (lane & 1);
+                    const T br = re[v], bi = im[v];
+                    re[v] = rot ? flip_sign(bi) : br;
+                    im[v] = rot ? br : bi;
+                } else if (h != 1) {
                     const T br = re[v], bi = im[v];
                     re[v] = br * wr + bi * wi;
                     im[v] = bi * wr - br * wi;
