@@ -141,6 +141,24 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
                         wts[pl * PS + k * WS + W2 - 1 - j] = hi;
                     }
                     __syncwarp();
+                    if (cnt == 1) {
+                        // a lone point (sparse cells, typical of FP64 plans): its products go
+                        // straight into the tile, one multiply-add per value instead of a product
+                        // and a separate add
+                        const T *pw = wts;
+                        T wz[W2];
+                        lds_vec<T, W2>(pw + (DW - 1) * WS, wz);
+#pragma unroll
+                        for (int t = 0; t < RPL; ++t) {
+                            if (!rvalid[t]) continue;
+                            const T rw = pw[ra[t]] * pw[WS + rb[t]];
+                            T *dst = tile + ((lc[0] + ra[t]) * TW + (lc[1] + rb[t])) * TW + lc[2];
+#pragma unroll
+                            for (int c = 0; c < W2; ++c) dst[c] = fma(rw, wz[c], dst[c]);
+                        }
+                        __syncwarp();
+                        continue;
+                    }
 #pragma unroll
                     for (int t0 = 0; t0 < RPL; t0 += RCH) {
                         T acc[RCH][W2];
