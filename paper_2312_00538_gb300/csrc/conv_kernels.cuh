@@ -141,8 +141,9 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
 
 template <typename T, int NOS>
 struct ConvCfg {
-    static constexpr int LS = NOS + 1;  // padded line stride in shared memory
-    static constexpr size_t smem = sizeof(T) * ((size_t)32 * LS + NOS + NOS);
+    static constexpr int LT = kConvLines;  // grid lines per CTA (at most)
+    static constexpr int LS = NOS + 1;     // padded line stride in shared memory
+    static constexpr size_t smem = sizeof(T) * ((size_t)LT * LS + NOS + NOS);
 };
 
 // Strides of window grids: element (u_0, .., u_{d-1}) at sum_k u_k n_os^{d-1-k}.
@@ -151,8 +152,9 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     using C = ConvCfg<T, NOS>;
     constexpr int VPL = NOS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LT = C::LT;
     T *buf = reinterpret_cast<T *>(smem_raw);
-    T *twr = buf + 32 * C::LS;
+    T *twr = buf + LT * C::LS;
     T *twi = twr + NOS / 2;
     T *d1 = twi + NOS / 2;
 
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     if (ti >= a.tile_end) return;
     const int r = blockIdx.y;
     const int4 tl = a.tiles[ti];
-    const int w = tl.x, p = tl.y, q0 = tl.z, ax = tl.w;
+    // tl.w: axis in the low byte; above it the tile's line count (0: up to LT lines)
+    const int w = tl.x, p = tl.y, q0 = tl.z, ax = tl.w & 255, tile_lines = tl.w >> 8;
     const DevWindow dw = a.dwin[w];
 
     for (int i = threadIdx.x; i < NOS / 2; i += blockDim.x) {
@@ -192,18 +195,18 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     const long long goff = (a.zero_offset ? 0 : dw.grid_off) + p * s_p;
     const T *in = reinterpret_cast<const T *>(a.in) + (size_t)r * a.grid_stride_rhs + goff;
     T *out = reinterpret_cast<T *>(a.out) + (size_t)r * a.grid_stride_rhs + goff;
-    const int nlines = DW == 1 ? 1 : min(32, NOS - q0);
+    const int nlines = DW == 1 ? 1 : min(tile_lines > 0 ? tile_lines : LT, NOS - q0);
 
-    for (int i = threadIdx.x; i < 32 * NOS; i += blockDim.x) {
+    for (int i = threadIdx.x; i < LT * NOS; i += blockDim.x) {
         int j, u;
-        if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % 32; u = i / 32; }
+        if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % LT; u = i / LT; }
         T val = T(0);
         if (j < nlines) val = in[(long long)u * s_ax + (long long)(q0 + j) * s_q];
         buf[j * C::LS + u] = val;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int pr = warp; pr < 16; pr += blockDim.x / 32) {
+    for (int pr = warp; pr < LT / 2; pr += blockDim.x / 32) {
         if (2 * pr >= nlines) break;
         T re[VPL], im[VPL];
 #pragma unroll
@@ -219,9 +222,9 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 32 * NOS; i += blockDim.x) {
+    for (int i = threadIdx.x; i < LT * NOS; i += blockDim.x) {
         int j, u;
-        if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % 32; u = i / 32; }
+        if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % LT; u = i / LT; }
         if (j < nlines) out[(long long)u * s_ax + (long long)(q0 + j) * s_q] = buf[j * C::LS + u];
     }
 }

@@ -518,7 +518,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     if (pass == 1) { qlo = wi.box_lo[0]; qhi = wi.box_hi[0]; }
                 }
                 for (int pp = plo; pp < phi; ++pp)
-                    for (int q = (qlo / 32) * 32; q < qhi; q += 32) ftiles.push_back(make_int4(w, pp, q, pass));
+                    for (int q = qlo; q < qhi; q += kConvLines)
+                        ftiles.push_back(make_int4(w, pp, q, pass | (std::min(kConvLines, qhi - q) << 8)));
                 wi.tile_end[pass] = (int)ftiles.size();
             }
         }
@@ -606,10 +607,12 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     return fail(ANOVA_ERR_CUDA, "plan check: grid box");
             (void)tw;
         }
-        for (const int4 &t : ftiles)
-            if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || t.z + 32 > nos || t.w < 0 ||
-                t.w >= p->win[t.x].dw)
+        for (const int4 &t : ftiles) {
+            const int ax = t.w & 255, lines = t.w >> 8;
+            if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || lines < 1 || lines > kConvLines ||
+                t.z + lines > nos || ax >= p->win[t.x].dw)
                 return fail(ANOVA_ERR_CUDA, "plan check: FFT tile");
+        }
     }
 
     // ------------------------------------------------------------------ upload tables
