@@ -24,7 +24,10 @@ constexpr int kWiMax = ANOVA_WI_MAX;  // points per spread work item (at most)
 #define ANOVA_F64_B 4
 #endif
 constexpr int kBinF64 = ANOVA_F64_B;   // cells per bin edge of FP64 plans (FP32: 4)
-constexpr int kConvLines = 16;         // grid lines per CTA of an FFT pass
+#ifndef ANOVA_CONV_LINES
+#define ANOVA_CONV_LINES 16
+#endif
+constexpr int kConvLines = ANOVA_CONV_LINES;  // grid lines per CTA of an FFT pass (even, <= 32)
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
