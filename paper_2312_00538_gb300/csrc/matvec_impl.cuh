@@ -600,11 +600,8 @@ anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_wi
             st = matvec_windows<T>(p, vr, nr, 0, p->P, part, g, gs, p->stream, p->dev_status + 1);
             if (st != ANOVA_OK) return st;
         }
-        const long long tot = p->n * nr;
-        const int nb = (int)std::min<long long>((tot + 255) / 256, 152LL * 16);
         cudaEvent_t e0 = stage_event(p);
-        k_window_sum<T><<<nb, 256, 0, p->stream>>>(part, kr, p->n, nr, p->P);
-        ANOVA_CUDA_TRY(cudaGetLastError());
+        ANOVA_CUDA_TRY(launch_window_sum<T>(part, kr, p->n, nr, p->P, p->stream));
         p->launches += 1;
         stage_record(p, STAGE_SUM, e0, stage_event(p));
     }

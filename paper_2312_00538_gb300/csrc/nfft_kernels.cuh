@@ -1368,17 +1368,48 @@ __global__ void __launch_bounds__(128) k_interp_direct(InterpDirectArgs<T> a) {
 }
 
 // ------------------------------------------------------------------ sum over windows
-template <typename T>
+// Kv[r][j] = sum over windows w (in order) of part[w][r][j]; blockIdx.y = r. VEC = 4: four
+// consecutive j per thread with 16-byte loads (n a multiple of 4 and Kv 16-byte aligned).
+template <typename T, int VEC>
 __global__ void k_window_sum(const T *__restrict__ part, T *__restrict__ Kv, long long n, int nrhs,
                              int P) {
-    const long long total = n * nrhs;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+    const int r = blockIdx.y;
+    const long long nv = n / VEC;
+    T *out = Kv + (size_t)r * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / n, j = i - r * n;
-        T s = T(0);
-        for (int w = 0; w < P; ++w) s += part[((size_t)w * nrhs + r) * n + j];
-        Kv[i] = s;
+        if constexpr (VEC == 4) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int w = 0; w < P; ++w) {
+                const float4 t = reinterpret_cast<const float4 *>(part + ((size_t)w * nrhs + r) * n)[i];
+                s.x += t.x;
+                s.y += t.y;
+                s.z += t.z;
+                s.w += t.w;
+            }
+            reinterpret_cast<float4 *>(out)[i] = s;
+        } else {
+            T s = T(0);
+            for (int w = 0; w < P; ++w) s += part[((size_t)w * nrhs + r) * n + i];
+            out[i] = s;
+        }
     }
+}
+
+// Launches k_window_sum with 16-byte loads where the sizes and alignment allow it (FP32).
+template <typename T>
+cudaError_t launch_window_sum(const T *part, T *Kv, long long n, int nrhs, int P, cudaStream_t st) {
+    auto blocks = [](long long items) {
+        return (int)std::max<long long>(1, std::min<long long>((items + 255) / 256, 152LL * 8));
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (n % 4 == 0 && reinterpret_cast<uintptr_t>(Kv) % 16 == 0 && reinterpret_cast<uintptr_t>(part) % 16 == 0) {
+            k_window_sum<T, 4><<<dim3(blocks(n / 4), nrhs), 256, 0, st>>>(part, Kv, n, nrhs, P);
+            return cudaGetLastError();
+        }
+    }
+    k_window_sum<T, 1><<<dim3(blocks(n), nrhs), 256, 0, st>>>(part, Kv, n, nrhs, P);
+    return cudaGetLastError();
 }
 
 }  // namespace anova
