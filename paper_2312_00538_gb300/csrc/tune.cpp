@@ -125,7 +125,7 @@ anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *wi
     std::vector<int> forks = fp64 && P >= 2 ? std::vector<int>{1, 0} : std::vector<int>{1};
     const Setting def{flags & 6, 16, 1};
     int candidates = 0;
-    // best setting of one plan; the first timing is the default setting
+    // the fastest candidate setting of one plan
     auto search = [&](anova_plan *pl, Setting *set, double *ms_out) -> anova_status {
         double bm = 0.0;
         for (int it : interps)
