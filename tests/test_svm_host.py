@@ -84,3 +84,18 @@ def test_request_footprint(ab):
     assert f(20_000, 3, o) < f(20_000, 3, hi)
     n, P, r = 50_000, 3, o.rank
     assert f(n, P, o) >= n * r * 12 + 8 * 4 * P * (2 * o.N_precise) ** 3
+
+
+def test_request_footprint_counts_transient_work(ab):
+    """The randomised Nystrom factor holds K G and K Q (2 n r doubles) while it is built, and the
+    autotuner holds a candidate FP64 plan beside the kept one: both raise the estimate."""
+    o = ab.svm_opts_default()
+    f = ab.svm_request_footprint
+    n, P = 30_000, 3
+    base = f(n, P, o)
+    ny = ab.svm_opts_default()
+    ny.precond = ab.NYSTROM_RANDOM
+    assert f(n, P, ny) >= base + 2 * n * ny.rank * 8
+    tu = ab.svm_opts_default()
+    tu.autotune = 1
+    assert f(n, P, tu) > base
