@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study", "predict"],
+    ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study", "predict",
+                                                                   "matvec_batch"],
                     help="matvec (default, the headline line) or ipm_batch (independent SVM "
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
@@ -579,6 +580,59 @@ def run_predict(args):
     return 0
 
 
+def run_matvec_batch(args):
+    """Matvecs of `count` independent problems of uneven size (workload-4 sizes and sigma grid,
+    three 3-D windows, FP32): one after another on one stream, against one CUDA graph with a
+    branch per problem (anova_matvec_batch_*). Inputs resident, L2 flushed between steps; the
+    value is points of all problems per second through the graph."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import config4
+    probs = config4(count=args.count, n_hi=args.n_max)
+    stream = torch.cuda.current_stream()
+    plans, vs, kvs = [], [], []
+    for q in probs:
+        p = ab.anova_nfft_plan(q["X"], q["windows"], q["sigma"], N=32, m=4, stream=stream)
+        v = torch.randn(q["X"].shape[0], device="cuda")
+        plans.append(p), vs.append(v), kvs.append(torch.empty_like(v))
+    total = sum(q["X"].shape[0] for q in probs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    batch = ab.anova_matvec_batch_create(plans, vs, kvs, stream=stream)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / args.steps
+
+    def sequential():
+        for p, v, k in zip(plans, vs, kvs):
+            ab.anova_matvec(p, v, k, 1)
+
+    seq_ms = timed(sequential)
+    graph_ms = timed(batch.run)
+    print(json.dumps({
+        "metric": "ANOVA-NFFT matvecs of independent problems, points/s", "value": total / (graph_ms / 1e3),
+        "unit": "pts/s", "ms_per_step": graph_ms, "steps": args.steps, "higher_is_better": True,
+        "data": "synthetic", "dtype": "f32",
+        "config": {"workload": "%d problems, n log-uniform [5e3, %d] (total %d points), d=9, windows=3x3D, "
+                               "sigma grid, N=32, m=4" % (len(probs), args.n_max, total),
+                   "l2": "flushed between steps (512 MiB write)"},
+        "sequential_ms": seq_ms, "graph_ms": graph_ms, "speedup": seq_ms / graph_ms}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -591,6 +645,8 @@ def main():
         return run_precond_study(args)
     if args.workload == "predict":
         return run_predict(args)
+    if args.workload == "matvec_batch":
+        return run_matvec_batch(args)
     return run_ours(args)
 
 

@@ -235,6 +235,27 @@ anova_status anova_nfft_plan_tuned(const double *points, int64_t n, int d, const
                                    int flags, void *cuda_stream, int nrhs, int reps,
                                    anova_tune_report *report, anova_plan_t *out);
 
+/*
+ * Batched matvecs of independent problems: the matvecs of `count` plans (different points,
+ * sizes, windows or precision; each plan at most once) captured as one CUDA graph, each plan's
+ * stage chain on its own branch, so one launch runs them all concurrently.
+ * anova_matvec_batch_create -- plans[k], v[k], Kv[k] (device, n_k x nrhs[k] of plan k's type,
+ *   column-major; nrhs may be NULL for 1 each) are fixed into the graph: a run reads v[k] and
+ *   overwrites Kv[k] as anova_matvec(plans[k], v[k], Kv[k], nrhs[k]) does, with identical
+ *   results. Runs each matvec once before capturing (Kv is written), on each plan's stream, and
+ *   synchronises. cuda_stream: the stream the graph is launched on (NULL = default stream).
+ *   The plans must outlive the batch and not have stage timing on. Errors: INVALID_ARG (NULL,
+ *   count outside [1, 4096], a plan twice, plans on several devices), OOM, CUDA.
+ * anova_matvec_batch_run -- one launch of the graph (asynchronous on the batch's stream).
+ * anova_matvec_batch_destroy -- frees the graph (NULL is ignored).
+ */
+typedef struct anova_batch *anova_batch_t;
+anova_status anova_matvec_batch_create(int count, anova_plan_t const *plans, const void *const *v,
+                                       void *const *Kv, const int *nrhs, void *cuda_stream,
+                                       anova_batch_t *out);
+anova_status anova_matvec_batch_run(anova_batch_t batch);
+void anova_matvec_batch_destroy(anova_batch_t batch);
+
 /* Plan facts. Any output pointer may be NULL. device_bytes = device memory the plan holds. */
 anova_status anova_plan_info(anova_plan_t plan, int64_t *n, int *P, int *n_os, int *flags,
                              int64_t *device_bytes);

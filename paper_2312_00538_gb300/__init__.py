@@ -63,6 +63,11 @@ _SIGNATURES = {
     "anova_nfft_plan_tuned": (_c_int, [_dp, _c_i64, _c_int, _ip, _c_int, _dp, _dp, _c_int, _c_int,
                                        _c_int, _vp, _c_int, _c_int, _vp, ctypes.POINTER(_vp)]),
     "anova_matvec": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "anova_matvec_batch_create": (_c_int, [_c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_vp), ctypes.POINTER(_c_int), _vp,
+                                           ctypes.POINTER(_vp)]),
+    "anova_matvec_batch_run": (_c_int, [_vp]),
+    "anova_matvec_batch_destroy": (None, [_vp]),
     "anova_model_create": (_c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
     "anova_model_eval": (_c_int, [_vp, _vp, _vp]),
     "anova_model_destroy": (None, [_vp]),
@@ -295,6 +300,41 @@ def anova_plan_info(plan):
 def anova_cross_matvec(source, target, w, f):
     """f (device, target points) = sum over windows and sources of w_i K(t_j, s_i)."""
     _check(lib().anova_cross_matvec(source.handle, target.handle, _dev_ptr(w), _dev_ptr(f)))
+
+
+class MatvecBatch:
+    """Owns an anova_batch_t (one CUDA graph over several plans' matvecs); keeps the plans and
+    vectors alive while it exists."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def run(self):
+        _check(lib().anova_matvec_batch_run(self.handle))
+
+    def destroy(self):
+        if self.handle:
+            lib().anova_matvec_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def anova_matvec_batch_create(plans, vs, kvs, nrhs=None, stream=None):
+    """One CUDA graph running anova_matvec(plans[k], vs[k], kvs[k], nrhs[k]) for every k."""
+    count = len(plans)
+    P = (_vp * count)(*[p.handle for p in plans])
+    V = (_vp * count)(*[_dev_ptr(v) for v in vs])
+    K = (_vp * count)(*[_dev_ptr(k) for k in kvs])
+    R = None if nrhs is None else (_c_int * count)(*[int(x) for x in nrhs])
+    h = _vp()
+    _check(lib().anova_matvec_batch_create(count, P, V, K, R, _stream_handle(stream), ctypes.byref(h)))
+    return MatvecBatch(h, (list(plans), list(vs), list(kvs)))
 
 
 class Model:

@@ -96,6 +96,15 @@ def test_model_calls_validate_before_device_work(ab):
     L.anova_model_destroy(None)
 
 
+def test_matvec_batch_validates_before_device_work(ab):
+    L = ab.lib()
+    h = ctypes.c_void_p()
+    assert L.anova_matvec_batch_create(0, None, None, None, None, None, ctypes.byref(h)) == ab.ANOVA_ERR_INVALID_ARG
+    assert L.anova_matvec_batch_create(2, None, None, None, None, None, ctypes.byref(h)) == ab.ANOVA_ERR_INVALID_ARG
+    assert L.anova_matvec_batch_run(None) == ab.ANOVA_ERR_INVALID_ARG
+    L.anova_matvec_batch_destroy(None)
+
+
 def test_unused_features_may_lie_outside_the_box(ab):
     # only the features named by a window must lie in [-0.2, 0.2]; validation passes this case
     # and fails later only for want of a device, which this CPU test tolerates

@@ -346,3 +346,38 @@ def test_tuned_plan_matches_default_and_oracle(env):
     ref64 = ok.anova_matvec(cfg["X"], cfg["windows"], cfg["sigma"], V2)
     for r in range(2):
         assert rel_l2(got64[:, r], ref64[:, r]) <= FP64_BAR
+
+
+def test_matvec_batch_graph_equals_separate_matvecs(env):
+    """One CUDA graph over plans of uneven size, window layout and precision gives, bitwise, each
+    plan's own matvec, on every launch."""
+    torch, ab = env
+    rng = np.random.default_rng(SEED_BASE + 90)
+    plans, vs, kvs, nrhs, refs = [], [], [], [], []
+    specs = [(3000, [[0, 1, 2], [3, 4, 5]], ab.ANOVA_FP32, 1), (17000, [[0, 1, 2]], ab.ANOVA_FP32, 2),
+             (800, [[0, -1, -1], [1, 2, -1]], ab.ANOVA_FP32, 1), (2500, [[0, 1, 2], [3, 4, 5]], ab.ANOVA_FP64, 1),
+             (40000, [[0, 1, 2], [3, 4, 5]], ab.ANOVA_FP32, 1)]
+    for n, W, fl, nr in specs:
+        X = minmax_scale(rng.standard_normal((n, 6)))
+        N, m = (32, 4) if fl == ab.ANOVA_FP32 else (64, 6)
+        p = ab.anova_nfft_plan(X, np.array(W), 0.7, N=N, m=m, flags=fl)
+        dt = torch.float32 if fl == ab.ANOVA_FP32 else torch.float64
+        v = torch.tensor(rng.standard_normal((nr, n)), dtype=dt, device="cuda")
+        if nr == 1:
+            v = v.reshape(-1)
+        ref = torch.empty_like(v)
+        ab.anova_matvec(p, v, ref, nr)
+        plans.append(p), vs.append(v), kvs.append(torch.empty_like(v)), nrhs.append(nr), refs.append(ref)
+    torch.cuda.synchronize()
+    batch = ab.anova_matvec_batch_create(plans, vs, kvs, nrhs)
+    for _ in range(2):
+        for k in kvs:
+            k.zero_()
+        batch.run()
+        torch.cuda.synchronize()
+        for p, k, ref in zip(plans, kvs, refs):
+            ab.anova_plan_check(p)
+            assert torch.equal(k, ref)
+    batch.destroy()
+    with pytest.raises(ab.AnovaError):
+        ab.anova_matvec_batch_create([plans[0], plans[0]], vs[:1] * 2, kvs[:1] * 2)
