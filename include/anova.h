@@ -155,13 +155,16 @@ anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void 
  *
  * Scratch: the spread kernel's partial tiles go to one static device array of 16 MiB that the
  * library declares at file scope; every GPU that loads the library holds it until the process
- * exits. The window's tiles must fit: a window needs (work items up to and including the window)
- * x (B + 2m - 1)^{d_l} elements (B = 4 for FP32 plans, 2 for FP64); a larger requirement returns
+ * exits. The window's tiles must fit: a window needs (its own spread work items)
+ * x (B + 2m - 1)^{d_l} elements (B = 4, the bin edge in cells); a larger requirement returns
  * ANOVA_ERR_INVALID_ARG with the sizes in the message (use anova_spread_grid then). The call
  * makes no cudaMalloc, cudaFree or other allocating call; it clears the caller's grid itself.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. All calls share the one
+ * that device current; make that first call before any stream capture. The address is kept per
+ * device ordinal for the life of the process: it does not survive cudaDeviceReset (or any other
+ * destruction of the device's primary context), after which this entry point must not be called
+ * again in that process. All calls share the one
  * array, which keeps the last call's tiles: calls that can overlap on the GPU (different
  * streams, plans or threads without ordering between them) race on it.
  * Arguments and errors as anova_spread_grid.
@@ -246,7 +249,13 @@ anova_status anova_nfft_plan_tuned(const double *points, int64_t n, int d, const
  *   synchronises. cuda_stream: the stream the graph is launched on (NULL = default stream).
  *   The plans must outlive the batch and not have stage timing on. Errors: INVALID_ARG (NULL,
  *   count outside [1, 4096], a plan twice, plans on several devices), OOM, CUDA.
+ *   The graph uses each plan's own workspace buffers (grids, tiles, per-window results) as they
+ *   were when it was captured. A plan's own calls and the batch's runs therefore share those
+ *   buffers: the caller orders them (same stream, or events). A later call on a plan with more
+ *   right-hand sides than the plan's workspace holds reallocates it; the batch then refuses to
+ *   run (INVALID_ARG) and must be created again.
  * anova_matvec_batch_run -- one launch of the graph (asynchronous on the batch's stream).
+ *   Errors: INVALID_ARG (NULL batch, or a plan's workspace reallocated since the capture), CUDA.
  * anova_matvec_batch_destroy -- frees the graph (NULL is ignored).
  */
 typedef struct anova_batch *anova_batch_t;

@@ -142,6 +142,8 @@ struct anova_plan {
     void *tiles = nullptr;        // T[nwi][ws_rhs][tile_vol]
     void *part = nullptr;         // T[P][ws_rhs][n]
     int64_t ws_bytes = 0;
+    uint64_t ws_gen = 0;          // bumped whenever the workspace buffers are freed, so that a
+                                  // batch graph that captured their addresses can refuse to run
     // host-call staging
     void *dv = nullptr, *dkv = nullptr;
     int stage_rhs = 0;

@@ -17,6 +17,10 @@ struct anova_batch {
     cudaStream_t stream = nullptr;  // the stream the graph is launched on (not owned)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // the graph holds the addresses of each plan's workspace as captured; a later call that
+    // grows a plan's workspace frees those buffers, which this generation check detects
+    std::vector<anova_plan *> plans;
+    std::vector<uint64_t> ws_gen;
 };
 
 namespace {
@@ -127,6 +131,8 @@ anova_status anova_matvec_batch_create(int count, anova_plan_t const *plans, con
         if (e_end != cudaSuccess) return cuda_fail(e_end, "cudaStreamEndCapture");
         b->graph = graph;
         ANOVA_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->plans.assign(plans, plans + count);
+        for (int k = 0; k < count; ++k) b->ws_gen.push_back(plans[k]->ws_gen);
         owned.b = nullptr;
         *out = b;
         return ANOVA_OK;
@@ -139,6 +145,12 @@ anova_status anova_matvec_batch_create(int count, anova_plan_t const *plans, con
 
 anova_status anova_matvec_batch_run(anova_batch_t batch) {
     if (!batch) return fail(ANOVA_ERR_INVALID_ARG, "batch is NULL");
+    for (size_t k = 0; k < batch->plans.size(); ++k)
+        if (batch->plans[k]->ws_gen != batch->ws_gen[k])
+            return fail(ANOVA_ERR_INVALID_ARG,
+                        "plan " + std::to_string(k) +
+                            " reallocated its workspace after the batch was captured (a later call used "
+                            "more right-hand sides); create the batch again");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != batch->device && cudaSetDevice(batch->device) != cudaSuccess)

@@ -2,7 +2,9 @@
 // anova_spread_grid) for callers that must not allocate device memory. Its scratch -- the
 // partial tiles that the spread kernel writes and the reduction kernels read -- lives in a
 // file-scope device array of fixed size instead of the plan's on-demand workspace.
+#include <cstdint>
 #include <mutex>
+#include <new>
 
 #include "matvec_impl.cuh"
 
@@ -37,16 +39,21 @@ template <typename T>
 anova_status spread_noalloc(anova_plan *p, int w, const void *v, void *grid) {
     const WindowInfo &wi = p->win[w];
     const size_t tv = (size_t)tile_volume<T>(p, wi.dw);
-    // work items are indexed plan-wide, so the tiles of this window end at wi_end
-    const size_t need = (size_t)wi.wi_end * tv * sizeof(T);
+    // only this window's work items [wi_begin, wi_end) need tiles
+    const size_t need = (size_t)(wi.wi_end - wi.wi_begin) * tv * sizeof(T);
     if (need > kNoAllocScratchBytes)
         return fail(ANOVA_ERR_INVALID_ARG,
                     "anova_spread_grid_noalloc: this window needs " + std::to_string(need) +
                         " bytes of scratch; the static scratch holds " +
                         std::to_string(kNoAllocScratchBytes) + " bytes (use anova_spread_grid)");
-    void *scratch = nullptr;
-    anova_status st = scratch_address(p->device, &scratch);
+    void *base = nullptr;
+    anova_status st = scratch_address(p->device, &base);
     if (st != ANOVA_OK) return st;
+    // the kernels address tiles by plan-wide work-item index; shifting the base by the window's
+    // first item puts that item's tile at the start of the array (no access below the array:
+    // every index the kernels use is >= wi_begin)
+    void *scratch = reinterpret_cast<void *>(reinterpret_cast<uintptr_t>(base) -
+                                             (uintptr_t)wi.wi_begin * tv * sizeof(T));
     cudaStream_t s = p->stream;
 
     SpreadArgs sa;
@@ -130,6 +137,8 @@ extern "C" anova_status anova_spread_grid_noalloc(anova_plan_t plan, int l, cons
                                                    : spread_noalloc<float>(plan, w, v, grid);
         if (prev != plan->device) cudaSetDevice(prev);
         return st;
+    } catch (const std::bad_alloc &) {
+        return fail(ANOVA_ERR_OOM, "host allocation failed");
     } catch (...) {
         return fail(ANOVA_ERR_INVALID_ARG, "unexpected exception");
     }

@@ -178,6 +178,7 @@ struct DevBuf {
 size_t elem_size(const anova_plan *p) { return p->prec == ANOVA_FP64 ? sizeof(double) : sizeof(float); }
 
 void release_workspace(anova_plan *p) {
+    if (p->grids || p->tiles || p->part) ++p->ws_gen;
     if (p->grids) cudaFree(p->grids);
     if (p->tiles) cudaFree(p->tiles);
     if (p->part) cudaFree(p->part);
@@ -188,7 +189,9 @@ void release_workspace(anova_plan *p) {
 
 anova_status ensure_workspace(anova_plan *p, int nrhs) {
     if (nrhs <= p->ws_rhs) return ANOVA_OK;
-    cudaError_t e = cudaStreamSynchronize(p->stream);
+    // the old buffers may still be in use by a batch graph launched on another stream, so the
+    // whole device is waited for before they are freed
+    cudaError_t e = (p->grids || p->tiles || p->part) ? cudaDeviceSynchronize() : cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     release_workspace(p);
     const size_t es = elem_size(p);

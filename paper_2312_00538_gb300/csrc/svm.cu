@@ -1,9 +1,13 @@
 // Interior point method for the kernel SVM dual (arXiv 2312.00538, Sec. 2, Algorithm 1) with
 // Newton systems (eq. (Newton)) solved by preconditioned MINRES (Secs. 3, 5) on the FP32
-// ANOVA-NFFT operator, refined against FP64-plan residuals. Vectors live on the device in FP64;
-// the host runs the scalar recurrences (dot products come back as per-block partial sums that
-// the host adds in a fixed order, so results are reproducible). Also exports the low-rank
-// preconditioner calls of anova_svm.h.
+// ANOVA-NFFT operator, refined against FP64-plan residuals. Vectors live on the device in FP64.
+// The Krylov recurrences run on the device too: one-thread kernels keep the scalars (Lanczos
+// beta, the Givens rotations, the residual estimate; for GMRES the Hessenberg column) in device
+// memory, dot products are per-block partial sums added in a fixed order (reproducible), and an
+// FP32 Krylov solve is one CUDA graph whose conditional while node runs the iterations until the
+// device-side convergence test clears its condition. The host only drives the Newton steps and
+// the FP64 refinement around each solve. Also exports the low-rank preconditioner calls of
+// anova_svm.h.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

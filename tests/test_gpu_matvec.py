@@ -381,3 +381,33 @@ def test_matvec_batch_graph_equals_separate_matvecs(env):
     batch.destroy()
     with pytest.raises(ab.AnovaError):
         ab.anova_matvec_batch_create([plans[0], plans[0]], vs[:1] * 2, kvs[:1] * 2)
+
+
+def test_matvec_batch_refuses_a_plan_whose_workspace_was_reallocated(env):
+    """A batch graph holds the addresses of its plans' workspaces. A later call with more
+    right-hand sides reallocates a plan's workspace; the batch must then refuse to run instead of
+    launching into freed memory, and a batch created again must run and match."""
+    torch, ab = env
+    rng = np.random.default_rng(SEED_BASE + 91)
+    X = minmax_scale(rng.standard_normal((3000, 6)))
+    p = ab.anova_nfft_plan(X, np.array([[0, 1, 2], [3, 4, 5]]), 0.7, N=32, m=4, flags=ab.ANOVA_FP32)
+    v = torch.tensor(rng.standard_normal(3000), dtype=torch.float32, device="cuda")
+    kv = torch.empty_like(v)
+    batch = ab.anova_matvec_batch_create([p], [v], [kv], [1])
+    batch.run()
+    torch.cuda.synchronize()
+    first = kv.clone()
+    v4 = torch.tensor(rng.standard_normal((4, 3000)), dtype=torch.float32, device="cuda")
+    kv4 = torch.empty_like(v4)
+    ab.anova_matvec(p, v4, kv4, 4)          # grows the plan's workspace from 1 to 4 columns
+    torch.cuda.synchronize()
+    with pytest.raises(ab.AnovaError) as ei:
+        batch.run()
+    assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG and "workspace" in str(ei.value)
+    batch.destroy()
+    batch = ab.anova_matvec_batch_create([p], [v], [kv], [1])
+    kv.zero_()
+    batch.run()
+    torch.cuda.synchronize()
+    assert torch.equal(kv, first)
+    batch.destroy()
