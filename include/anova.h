@@ -299,6 +299,18 @@ anova_status anova_plan_stage_times(anova_plan_t plan, double *ms, int64_t *laun
  */
 anova_status anova_plan_check(anova_plan_t plan);
 
+/*
+ * anova_plan_set_wait_limit -- failure-detection hook: the number of polls each chunk's
+ * tensor-core completion wait in the FP32 3-D interpolation makes before it gives up (default
+ * 2^22, about a second; polls < 0 restores it, larger values are clamped to it). 0 makes every
+ * such wait give up without polling, so the kernel takes its timeout path at its first chunk:
+ * it sets the plan's flag (anova_plan_check then returns ANOVA_ERR_TIMEOUT), still waits with
+ * the full limit for the products it started before it frees its tensor memory, and returns.
+ * The results of calls made under a lowered limit are not valid. Synchronises the stream.
+ * The paper has no counterpart (it concerns the kernels' own failure handling).
+ */
+anova_status anova_plan_set_wait_limit(anova_plan_t plan, int64_t polls);
+
 /* Release a plan and its device memory (NULL is ignored). Synchronises its stream. */
 void anova_plan_destroy(anova_plan_t plan);
 

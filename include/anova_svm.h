@@ -65,11 +65,31 @@ anova_status lowrank_factor(lowrank_t lr, double *L);
 
 /*
  * lowrank_precond_set_theta -- prepare the Woodbury core for one interior point step:
- * M = I + L^T Theta^{-1} L (FP64 accumulation from an FP32 copy of L), its Cholesky factor,
- * and the Schur value s = y^T A^{-1} y. theta, y: device, n doubles; theta > 0, y in {-1, +1}.
- * Errors: BREAKDOWN if M or s is not positive. Synchronises the stream.
+ * M = I + L^T Theta^{-1} L (from an FP32 copy of L, FP64-accurate; see lowrank_set_core_path),
+ * its Cholesky factor, and the Schur value s = y^T A^{-1} y. theta, y: device, n doubles;
+ * theta > 0, y in {-1, +1}. Errors: BREAKDOWN if M or s is not positive, TIMEOUT if a bounded
+ * tensor-core wait ran out. Synchronises the stream.
  */
 anova_status lowrank_precond_set_theta(lowrank_t lr, const double *theta, const double *y);
+
+/*
+ * Computing path of the Woodbury core M = I + L^T Theta^{-1} L in lowrank_precond_set_theta.
+ *   LOWRANK_CORE_TENSOR: on the tensor cores with FP64 accuracy (rank <= 256). A = Theta^{-1/2} L
+ *     is split column by column into nine exact bf16 integer slices of 6 bits (error-free
+ *     splitting: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012); slice products are summed
+ *     exactly in the FP32 accumulator over 4096-row chunks and the chunk sums exactly in FP64, so M
+ *     agrees with an FP64 evaluation to about 1e-15 of its norm; deterministic.
+ *   LOWRANK_CORE_SIMT: FP64 tiles on the FP64 pipe (any rank).
+ *   LOWRANK_CORE_AUTO (default): the tensor cores when rank <= 256, else the FP64 pipe.
+ * lowrank_set_core_path -- selects the path for later set_theta calls. Errors: INVALID_ARG (bad
+ *   path, or LOWRANK_CORE_TENSOR with rank > 256).
+ * lowrank_core -- copies the core M of the last set_theta (before its factorisation; device,
+ *   rank x rank row-major doubles; M may be NULL) and reports the path it took. Synchronous.
+ *   Errors: INVALID_ARG (NULL lr, or no set_theta yet).
+ */
+enum { LOWRANK_CORE_AUTO = 0, LOWRANK_CORE_SIMT = 1, LOWRANK_CORE_TENSOR = 2 };
+anova_status lowrank_set_core_path(lowrank_t lr, int path);
+anova_status lowrank_core(lowrank_t lr, double *M, int *path_used);
 
 /*
  * lowrank_precond_apply -- x = blockdiag(A^, s)^{-1} g for the saddle system of size n + 1:
@@ -195,7 +215,10 @@ anova_status svm_ipm_solve_batch(svm_problem *problems, int count, double tol,
  * Requests (svm_problem, whose input and output buffers must stay valid until the request
  * completes) are queued by svm_server_submit and started in arrival order as soon as a worker is
  * free AND the device-memory estimate of the request fits in `hbm_budget_bytes` together with the
- * requests already running (a request larger than the whole budget runs alone). While a solve
+ * requests already running (a request larger than the whole budget runs alone). While the oldest
+ * queued request does not fit, the oldest younger request that fits starts instead (backfill); the
+ * same oldest request is passed at most 4 times, after which nothing younger starts until it has
+ * started (a bound on its wait for memory). While a solve
  * runs, its plans, grids, preconditioner and iterates stay on the device; solves on different
  * workers overlap on the GPU. Each result is bitwise the one svm_ipm_solve gives alone with the
  * same opts. Latency of a request = completion time - submission time.
@@ -207,6 +230,7 @@ typedef struct {
     int64_t reserved_bytes;       /* device-memory estimate of the running requests */
     int64_t peak_reserved_bytes;  /* the largest reserved_bytes seen */
     double p50_latency_ms, p99_latency_ms, mean_latency_ms;  /* over completed requests */
+    int64_t backfilled;           /* requests started ahead of an older one that did not fit */
 } svm_server_stats;
 
 anova_status svm_server_create(const svm_opts *opts, double tol, int slots, int64_t hbm_budget_bytes,

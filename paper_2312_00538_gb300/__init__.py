@@ -81,6 +81,7 @@ _SIGNATURES = {
                                  ctypes.POINTER(_c_int), _lp]),
     "anova_plan_destroy": (None, [_vp]),
     "anova_plan_check": (_c_int, [_vp]),
+    "anova_plan_set_wait_limit": (_c_int, [_vp, _c_i64]),
     "anova_cross_matvec": (_c_int, [_vp, _vp, _vp, _vp]),
     "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
@@ -91,6 +92,8 @@ _SIGNATURES = {
     "lowrank_factor": (_c_int, [_vp, _vp]),
     "lowrank_precond_set_theta": (_c_int, [_vp, _vp, _vp]),
     "lowrank_precond_apply": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lowrank_set_core_path": (_c_int, [_vp, _c_int]),
+    "lowrank_core": (_c_int, [_vp, _vp, ctypes.POINTER(_c_int)]),
     "lowrank_destroy": (None, [_vp]),
     "svm_opts_default": (None, [_vp]),
     "svm_ipm_solve": (_c_int, [_dp, _c_i64, _c_int, _dp, _c_dbl, _c_dbl, _vp, _dp, _dp, _vp]),
@@ -372,6 +375,11 @@ def anova_plan_check(plan):
     _check(lib().anova_plan_check(plan.handle))
 
 
+def anova_plan_set_wait_limit(plan, polls):
+    """Polls of each tensor-core completion wait before it gives up (negative: the default)."""
+    _check(lib().anova_plan_set_wait_limit(plan.handle, int(polls)))
+
+
 def anova_plan_destroy(plan):
     plan.destroy()
 
@@ -487,6 +495,21 @@ def lowrank_precond_set_theta(lr, theta, y):
     _check(lib().lowrank_precond_set_theta(lr.handle, _dev_ptr(theta), _dev_ptr(y)))
 
 
+LOWRANK_CORE_AUTO, LOWRANK_CORE_SIMT, LOWRANK_CORE_TENSOR = 0, 1, 2
+
+
+def lowrank_set_core_path(lr, path):
+    _check(lib().lowrank_set_core_path(lr.handle, int(path)))
+
+
+def lowrank_core(lr, M=None):
+    """Copies the Woodbury core of the last set_theta into M (device, rank x rank) if given;
+    returns the path it took (LOWRANK_CORE_SIMT or LOWRANK_CORE_TENSOR)."""
+    used = _c_int()
+    _check(lib().lowrank_core(lr.handle, None if M is None else _dev_ptr(M), ctypes.byref(used)))
+    return used.value
+
+
 def lowrank_precond_apply(lr, theta, y, g, x):
     _check(lib().lowrank_precond_apply(lr.handle, _dev_ptr(theta), _dev_ptr(y), _dev_ptr(g),
                                        _dev_ptr(x)))
@@ -578,7 +601,7 @@ class svm_server_stats(ctypes.Structure):
                 ("running", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("reserved_bytes", ctypes.c_int64), ("peak_reserved_bytes", ctypes.c_int64),
                 ("p50_latency_ms", ctypes.c_double), ("p99_latency_ms", ctypes.c_double),
-                ("mean_latency_ms", ctypes.c_double)]
+                ("mean_latency_ms", ctypes.c_double), ("backfilled", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

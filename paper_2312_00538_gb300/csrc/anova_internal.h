@@ -31,6 +31,7 @@ constexpr int kConvLines = ANOVA_CONV_LINES;  // grid lines per CTA of an FFT pa
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
+constexpr int kStatusAlloc = 128;      // ints of a plan's status/counter block (>= 1 + 3 x 32)
 
 // ----------------------------------------------------------------------------- host maths
 double kb_beta();
@@ -123,8 +124,9 @@ struct anova_plan {
     void *D1br = nullptr;         // T[P][3][n_os]: deconvolution diagonal per axis, bit-reversed
     void *tw = nullptr;           // T[n_os]: twiddles (re, im) pairs for k < n_os/2
     int *dev_status = nullptr;    // [0]: kernel-side error bits (a bounded tensor-core wait ran
-                                  // out); [1 + 16 k + r]: work counter of RHS r of a persistent
-                                  // launch on window stream k (64 ints)
+                                  // out); [1 + 32 k + r] / [1 + 32 k + 16 + r]: work and exit
+                                  // counters of RHS r of a persistent launch on window stream k
+                                  // (kStatusAlloc ints)
     int sm_count = 0;
     // windows of one matvec run concurrently on these streams (forked from and joined back to
     // `stream`); window w uses aux[w % kAuxStreams] and work-counter block w % kAuxStreams
@@ -134,6 +136,8 @@ struct anova_plan {
     int wi_max = anova::kWiMax;   // points per work item (at most); set at plan creation
     int rhs_chunk = 16;           // right-hand sides per pass of the multi-RHS matvec (1..16)
     int fork_windows = 1;         // FP64: run windows of one dimension group on the aux streams
+    unsigned wait_polls = 1u << 22;  // polls of a bounded tensor-core completion wait (about a
+                                     // second); anova_plan_set_wait_limit lowers it
     int64_t static_bytes = 0;
 
     // workspace, grown on demand

@@ -334,6 +334,17 @@ anova_status anova_plan_check(anova_plan_t plan) {
     });
 }
 
+anova_status anova_plan_set_wait_limit(anova_plan_t plan, int64_t polls) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        DeviceGuard g(plan->device);
+        ANOVA_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+        const int64_t full = (int64_t)1 << 22;
+        plan->wait_polls = (unsigned)(polls < 0 ? full : std::min(polls, full));
+        return ANOVA_OK;
+    });
+}
+
 void anova_plan_destroy(anova_plan_t plan) {
     if (!plan) return;
     DeviceGuard g(plan->device);

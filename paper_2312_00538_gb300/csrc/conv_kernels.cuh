@@ -149,6 +149,8 @@ struct ConvCfg {
 // Strides of window grids: element (u_0, .., u_{d-1}) at sum_k u_k n_os^{d-1-k}.
 template <typename T, int NOS, int DW>
 __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = ConvCfg<T, NOS>;
     constexpr int VPL = NOS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];

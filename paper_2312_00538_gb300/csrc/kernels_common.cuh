@@ -6,7 +6,52 @@
 
 #include "anova_internal.h"
 
+#ifndef ANOVA_PDL
+#define ANOVA_PDL 1
+#endif
+
 namespace anova {
+
+// ---------------------------------------------------------------- programmatic dependent launch
+// The kernels of one matvec are launched with programmatic stream serialisation: a kernel's CTAs
+// may be scheduled while its predecessor in the stream is still finishing, and each kernel waits
+// (griddepcontrol.wait: the predecessor has completed and its writes are visible) before it
+// reads anything, then lets its own successor be scheduled. Launch latency and the ramp of the
+// next grid overlap the tail of the previous one. A kernel launched without the attribute
+// passes the wait at once.
+__device__ __forceinline__ void pdl_wait() {
+#if ANOVA_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_trigger() {
+#if ANOVA_PDL
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+// Launches kern<<<grid, block, smem, st>>>(args...), with programmatic stream serialisation when
+// it is compiled in (every kernel launched here calls pdl_wait() before its first dependent read).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args &&...args) {
+#if ANOVA_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+#else
+    kern<<<grid, block, smem, st>>>(static_cast<KArgs>(args)...);
+    return cudaGetLastError();
+#endif
+}
 
 // Window polynomial coefficients (FP32 kernels) and Kaiser-Bessel constants (FP64 kernels),
 // passed by value so that they live in the kernel-parameter constant bank.

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "anova_internal.h"
+#include "../../include/anova_svm.h"
 #include "lowrank_internal.h"
 
 namespace anova {
@@ -639,7 +640,8 @@ void lowrank_release(lowrank *lr) {
     if (!lr) return;
     void *bufs[] = {lr->L64, lr->L32, lr->d, lr->piv_dev, lr->dpiv, lr->stop, lr->partial, lr->M,
                     lr->u, lr->z, lr->upart, lr->tiles, lr->cpart, lr->info, lr->tmp,
-                    lr->dpart, lr->schur, lr->Wl, lr->Wc, lr->tmp2, lr->dinv, lr->itheta, lr->hbuf};
+                    lr->dpart, lr->schur, lr->Wl, lr->Wc, lr->tmp2, lr->dinv, lr->itheta, lr->hbuf,
+                    lr->Mcore, lr->tc_Q, lr->tc_I, lr->tc_srow, lr->tc_srow32, lr->tc_cmax, lr->tc_work, lr->tc_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete lr;
@@ -796,6 +798,7 @@ static anova_status lowrank_finish(lowrank *lr) {
     }
     lr->napply = (int)((n + kApplyRows - 1) / kApplyRows);
     if ((cudaMalloc(&lr->M, sizeof(double) * rank * rank)) != cudaSuccess ||
+        (cudaMalloc(&lr->Mcore, sizeof(double) * rank * rank)) != cudaSuccess ||
         (cudaMalloc(&lr->u, sizeof(double) * rank)) != cudaSuccess ||
         (cudaMalloc(&lr->z, sizeof(double) * rank)) != cudaSuccess ||
 
@@ -967,9 +970,21 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
     const long long n = lr->n;
     const int r = lr->rank;
     k_recip<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(theta, n, lr->itheta);
-    k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, lr->itheta, n, r, lr->core_rows,
-                                                                   (const int2 *)lr->tiles, lr->cpart);
-    k_core_sum<<<lr->ntiles, 256, 0, st>>>(lr->cpart, lr->nchunks, lr->ntiles, (const int2 *)lr->tiles, r, lr->M);
+    // M = I + L^T Theta^-1 L: exact-slice products on the tensor cores (csrc/core_tc.cu) where the
+    // rank allows it, else FP64 tiles on the FP64 pipe
+    const bool tensor = lr->core_path == LOWRANK_CORE_TENSOR ||
+                        (lr->core_path == LOWRANK_CORE_AUTO && core_tc_supported(lr));
+    if (tensor) {
+        if (!core_tc_supported(lr)) return fail(ANOVA_ERR_INVALID_ARG, "tensor-core Woodbury core needs rank <= 256");
+        anova_status cs = core_tc(lr);
+        if (cs != ANOVA_OK) return cs;
+    } else {
+        k_core_partial<<<dim3(lr->ntiles, lr->nchunks), 256, 0, st>>>(lr->L32, lr->itheta, n, r, lr->core_rows,
+                                                                       (const int2 *)lr->tiles, lr->cpart);
+        k_core_sum<<<lr->ntiles, 256, 0, st>>>(lr->cpart, lr->nchunks, lr->ntiles, (const int2 *)lr->tiles, r, lr->M);
+    }
+    lr->core_used = tensor ? LOWRANK_CORE_TENSOR : LOWRANK_CORE_SIMT;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(lr->Mcore, lr->M, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
     if (r <= kSmemCholMax) {
         static const cudaError_t attr =
             cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -980,9 +995,11 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
         k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info, lr->dinv);
     }
     ANOVA_CUDA_TRY(cudaGetLastError());
-    int info = 0;
+    int info = 0, tc_status = 0;
     ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (tensor) ANOVA_CUDA_TRY(cudaMemcpyAsync(&tc_status, lr->tc_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tc_status != 0) return fail(ANOVA_ERR_TIMEOUT, "a bounded tensor-core wait in the Woodbury core ran out");
     if (info != 0) return fail(ANOVA_ERR_BREAKDOWN, "Woodbury core is not positive definite");
     k_tri_inv<<<r, 32, sizeof(double) * r, st>>>(lr->M, lr->dinv, r, lr->Wl, lr->Wc);
     ANOVA_CUDA_TRY(cudaGetLastError());

@@ -33,6 +33,21 @@ struct lowrank {
     int ntiles = 0, nchunks = 0, napply = 0;
     double schur_host = 0.0;
     bool core_ready = false;
+    double *Mcore = nullptr;     // the core M of the last set_theta before its factorisation (r x r)
+    int core_path = 0;           // LOWRANK_CORE_AUTO / _SIMT / _TENSOR
+    int core_used = 0;           // the path the last set_theta took (LOWRANK_CORE_SIMT / _TENSOR)
+    // tensor-core core (csrc/core_tc.cu): integer slices of Theta^{-1/2} L, the per-row scales
+    // Theta^{-1/2}, per-column maxima (double bits), exact integer accumulators of the slice
+    // products, the CTA work list, an error word
+    void *tc_Q = nullptr;
+    double *tc_I = nullptr;
+    double *tc_srow = nullptr;
+    float *tc_srow32 = nullptr;
+    unsigned *tc_cmax = nullptr;
+    void *tc_work = nullptr;
+    int *tc_status = nullptr;
+    long long tc_np = 0;
+    int tc_RP = 0, tc_nwork = 0;
 };
 
 namespace anova {
@@ -42,4 +57,6 @@ anova_status lowrank_apply_impl(lowrank *lr, const double *theta, const double *
 anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, const double *g, double *x,
                             bool with_schur);
 void lowrank_release(lowrank *lr);
+bool core_tc_supported(const lowrank *lr);
+anova_status core_tc(lowrank *lr);
 }  // namespace anova

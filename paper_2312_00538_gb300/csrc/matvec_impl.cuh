@@ -56,8 +56,7 @@ cudaError_t launch_spread_t(const SpreadArgs &a, int nblocks, int nrhs, cudaStre
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(nblocks, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
 template <typename T, int DW, int M>
@@ -68,8 +67,7 @@ cudaError_t launch_interp_t(const InterpArgs &a, int nseg, int nrhs, cudaStream_
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3((nseg + NW - 1) / NW, nrhs), NW * 32, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3((nseg + NW - 1) / NW, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
 template <typename T, int NOS, int DW>
@@ -79,8 +77,7 @@ cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t 
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(ntiles, nrhs), 256, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(ntiles, nrhs), dim3(256), C::smem, st, a);
 }
 
 // CTAs of `kern` (threads per CTA, dynamic shared memory) that fit on one SM at once, from its
@@ -111,8 +108,7 @@ cudaError_t launch_spread3_x2(const SpreadArgs &a, int nblocks, int nrhs, cudaSt
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(nblocks, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
 template <int M>
@@ -123,14 +119,13 @@ cudaError_t launch_interp3_x2(const InterpWiArgs &a, int nblocks, int nrhs, cuda
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(nblocks, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
-template <int M>
-cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm_count, cudaStream_t st) {
+template <int M, bool PARAM_WAIT>
+cudaError_t launch_interp3_tc_t(const InterpWiArgs &a, int nwork, int nrhs, int sm_count, cudaStream_t st) {
     using C = InterpTcCfg<M, Prec<float>::B>;
-    auto kern = k_interp3_tc<M, Prec<float>::B>;
+    auto kern = k_interp3_tc<M, Prec<float>::B, PARAM_WAIT>;
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
@@ -141,12 +136,17 @@ cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm
         cudaError_t e = resident_ctas(kern, 128, C::smem, (int)(512 / C::TMEM_COLS), &per_sm);
         if (e != cudaSuccess) return e;
     }
-    // persistent CTAs take work items from the per-RHS counters a.counters[r]
-    cudaError_t e = cudaMemsetAsync(a.counters, 0, sizeof(int) * kStatusCounters, st);
-    if (e != cudaSuccess) return e;
+    // persistent CTAs take work items from the per-RHS counters a.counters[r] (zero at every
+    // launch: the kernel's last CTA resets them)
     const int nblocks = std::max(1, std::min(nwork, per_sm * std::max(sm_count, 1)));
-    kern<<<dim3(nblocks, nrhs), 128, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(nblocks, nrhs), dim3(128), C::smem, st, a);
+}
+
+template <int M>
+cudaError_t launch_interp3_tc(const InterpWiArgs &a, int nwork, int nrhs, int sm_count, cudaStream_t st) {
+    return a.wait_polls == InterpTcCfg<M, Prec<float>::B>::kMaxPolls
+               ? launch_interp3_tc_t<M, false>(a, nwork, nrhs, sm_count, st)
+               : launch_interp3_tc_t<M, true>(a, nwork, nrhs, sm_count, st);
 }
 
 template <typename T, int DW, int M>
@@ -157,8 +157,7 @@ cudaError_t launch_interp_bin_t(const InterpBinArgs<T> &a, int nblocks, int nrhs
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
-    kern<<<dim3(nblocks, nrhs), NW * 32, C::smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(kern, dim3(nblocks, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
 template <typename T, int DW>
@@ -197,13 +196,12 @@ cudaError_t dispatch_interp_direct_m(int m, const InterpDirectArgs<T> &a, int nr
     const long long cnt = a.q_end - a.q_begin;
     const dim3 grid((unsigned)((cnt + 127) / 128), nrhs);
     switch (m) {
-        case 3: k_interp_direct<T, DW, 3><<<grid, 128, 0, st>>>(a); break;
-        case 4: k_interp_direct<T, DW, 4><<<grid, 128, 0, st>>>(a); break;
-        case 5: k_interp_direct<T, DW, 5><<<grid, 128, 0, st>>>(a); break;
-        case 6: k_interp_direct<T, DW, 6><<<grid, 128, 0, st>>>(a); break;
+        case 3: return launch_k(k_interp_direct<T, DW, 3>, grid, dim3(128), 0, st, a);
+        case 4: return launch_k(k_interp_direct<T, DW, 4>, grid, dim3(128), 0, st, a);
+        case 5: return launch_k(k_interp_direct<T, DW, 5>, grid, dim3(128), 0, st, a);
+        case 6: return launch_k(k_interp_direct<T, DW, 6>, grid, dim3(128), 0, st, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <typename T>
@@ -343,8 +341,7 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
     ba.tv_max = tile_volume<T>(p, dw);
     if (ba.nmbins > 0) {
         const int chunks = (ba.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
-        k_bin_reduce<T><<<dim3(ba.nmbins * chunks, nrhs), 256, 0, st>>>(ba);
-        ANOVA_CUDA_TRY(cudaGetLastError());
+        ANOVA_CUDA_TRY(launch_k(k_bin_reduce<T>, dim3(ba.nmbins * chunks, nrhs), dim3(256), 0, st, ba));
         p->launches += 1;
     }
     ReduceArgs ra;
@@ -366,10 +363,8 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
     const long long vol = ra.box_cum[a1 - a0];
     if (vol > 0) {
         const int nb = (int)((vol + 255) / 256);
-        if (dw == 3) k_reduce<T, 3><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
-        else if (dw == 2) k_reduce<T, 2><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
-        else k_reduce<T, 1><<<dim3(nb, nrhs), 256, 0, st>>>(ra);
-        ANOVA_CUDA_TRY(cudaGetLastError());
+        auto kr = dw == 3 ? k_reduce<T, 3> : dw == 2 ? k_reduce<T, 2> : k_reduce<T, 1>;
+        ANOVA_CUDA_TRY(launch_k(kr, dim3(nb, nrhs), dim3(256), 0, st, ra));
         p->launches += 1;
     }
     return ANOVA_OK;
@@ -406,6 +401,7 @@ anova_status interp_stage(anova_plan *p, const Group &gr, int a0, int a1, int w0
         xa.part_w0 = w0;
         xa.wp = wp;
         xa.status = p->dev_status;
+        xa.wait_polls = p->wait_polls;
         xa.counters = counters;
         xa.order = order;
         cudaError_t e;

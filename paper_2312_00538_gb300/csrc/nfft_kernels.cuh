@@ -57,6 +57,8 @@ struct SpreadCfg {
 
 template <typename T, int DW, int M, int B, int NWARP>
 __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = SpreadCfg<T, DW, M, B, NWARP>;
     using G = typename C::G;
     constexpr int W2 = G::W2, RPL = G::RPL, WS = G::WS, PS = G::PSTRIDE, TW = C::TW;
@@ -298,6 +300,8 @@ struct SpreadX2Cfg {
 
 template <int M, int B, int NWARP, int LPP>
 __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(SpreadArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = SpreadX2Cfg<M, B, NWARP, LPP>;
     constexpr int W2 = C::W2, RPL = C::RPL, S = C::S, TW = C::TW, PS = C::PS;
     constexpr int PPS = 32 / LPP;  // points per warp step
@@ -540,6 +544,8 @@ constexpr int kBinReduceChunk = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bin_reduce(BinReduceArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T part[8][kBinReduceChunk];
     const int chunks = (a.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
     const int b = a.mb_begin + blockIdx.x / chunks;
@@ -578,6 +584,8 @@ struct ReduceArgs {
 
 template <typename T, int DW>
 __global__ void __launch_bounds__(256) k_reduce(ReduceArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.y;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int nw = a.w_end - a.w_begin;
@@ -652,6 +660,8 @@ struct InterpCfg {
 
 template <typename T, int DW, int M, int NWARP>
 __global__ void __launch_bounds__(NWARP * 32) k_interp(InterpArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = InterpCfg<T, DW, M, NWARP>;
     using G = typename C::G;
     constexpr int W2 = G::W2;
@@ -775,6 +785,9 @@ struct InterpWiArgs {
     int nrhs, wi_begin, wi_end, n_os, part_w0;
     WinParams wp;
     int *status;             // error bits (tensor-core path: a bounded wait ran out)
+    unsigned wait_polls;     // tensor-core path: polls of each chunk's completion wait before it
+                             // gives up (the drain before the accumulators are freed always
+                             // uses the full limit)
     const int *order;        // persistent kernels: work items of each window, largest first
     int *counters;           // persistent kernels: per-RHS work counters (zeroed before the launch)
 };
@@ -789,6 +802,8 @@ struct InterpX2Cfg {
 
 template <int M, int B, int NWARP>
 __global__ void __launch_bounds__(NWARP * 32) k_interp3_x2(InterpWiArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = InterpX2Cfg<M, B, NWARP>;
     constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS;
     static_assert(W2 % 4 == 0, "pairs along the last axis");
@@ -914,11 +929,21 @@ struct InterpTcCfg {
     static_assert(TW <= KC, "a column fits in two K = 8 steps");
 };
 
-// per-RHS work counters of the persistent tensor-core kernels live after the status word
-constexpr int kStatusCounters = 16;
+// per-RHS counters of the persistent tensor-core kernels live after the status word, in blocks
+// of kStatusCounters ints: 16 work counters (next work item per RHS), then 16 exit counters
+// (CTAs that have finished, per RHS). The last CTA of a RHS to finish puts both back to zero,
+// so every launch finds them zeroed without a memset in the stream.
+constexpr int kStatusCounters = 32;
+constexpr int kStatusInts = 1 + 3 * kStatusCounters;
+static_assert(kStatusInts <= kStatusAlloc, "status block holds three counter blocks");
 
-template <int M, int B>
+// PARAM_WAIT: the chunk completion waits take their poll bound from a.wait_polls (the
+// failure-detection hook) instead of the compile-time bound. Only launched when the bound was
+// lowered: a runtime bound in the hot loop measured about 11 % slower.
+template <int M, int B, bool PARAM_WAIT>
 __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(InterpWiArgs a) {
+    pdl_wait();
+    pdl_trigger();
     using C = InterpTcCfg<M, B>;
     constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS, KC = C::KC;
     static_assert(W2 == 8 && C::NCOL == 64 && B == 4, "layout written for m = 4, B = 4");
@@ -1103,7 +1128,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
             float wx[W2], wy[W2];
             Weights<float, M>::eval(rw.f[0], a.wp, wx);
             Weights<float, M>::eval(rw.f[1], a.wp, wy);
-            if (!tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, C::kMaxPolls)) {
+            if (!tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, PARAM_WAIT ? a.wait_polls : C::kMaxPolls)) {
                 failed = true;
                 return;
             }
@@ -1182,6 +1207,15 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     }
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+    if (t == 0) {
+        // every CTA has taken its last work item before it counts itself out; the last one out
+        // resets this RHS's counters for the next launch
+        __threadfence();
+        if (atomicAdd(&a.counters[16 + r], 1) == (int)gridDim.x - 1) {
+            atomicExch(&a.counters[r], 0);
+            atomicExch(&a.counters[16 + r], 0);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ interpolation, any dims
@@ -1213,6 +1247,8 @@ struct InterpBinCfg {
 
 template <typename T, int DW, int M, int B, int NWARP>
 __global__ void __launch_bounds__(NWARP * 32) k_interp_bin(InterpBinArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     using C = InterpBinCfg<T, DW, M, B, NWARP>;
     constexpr int W2 = C::W2, TW = C::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1312,6 +1348,8 @@ struct InterpDirectArgs {
 
 template <typename T, int DW, int M>
 __global__ void __launch_bounds__(128) k_interp_direct(InterpDirectArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int W2 = 2 * M;
     const int r = blockIdx.y;
     const long long q = a.q_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1373,6 +1411,8 @@ __global__ void __launch_bounds__(128) k_interp_direct(InterpDirectArgs<T> a) {
 template <typename T, int VEC>
 __global__ void k_window_sum(const T *__restrict__ part, T *__restrict__ Kv, long long n, int nrhs,
                              int P) {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.y;
     const long long nv = n / VEC;
     T *out = Kv + (size_t)r * n;
@@ -1404,12 +1444,10 @@ cudaError_t launch_window_sum(const T *part, T *Kv, long long n, int nrhs, int P
     };
     if constexpr (sizeof(T) == 4) {
         if (n % 4 == 0 && reinterpret_cast<uintptr_t>(Kv) % 16 == 0 && reinterpret_cast<uintptr_t>(part) % 16 == 0) {
-            k_window_sum<T, 4><<<dim3(blocks(n / 4), nrhs), 256, 0, st>>>(part, Kv, n, nrhs, P);
-            return cudaGetLastError();
+            return launch_k(k_window_sum<T, 4>, dim3(blocks(n / 4), nrhs), dim3(256), 0, st, part, Kv, n, nrhs, P);
         }
     }
-    k_window_sum<T, 1><<<dim3(blocks(n), nrhs), 256, 0, st>>>(part, Kv, n, nrhs, P);
-    return cudaGetLastError();
+    return launch_k(k_window_sum<T, 1>, dim3(blocks(n), nrhs), dim3(256), 0, st, part, Kv, n, nrhs, P);
 }
 
 }  // namespace anova

@@ -16,7 +16,7 @@ namespace anova {
 
 namespace {
 
-constexpr int kSortTile = 4096;
+constexpr int kSortTile = 1024;  // keys per histogram tile (one scatter warp each)
 
 __global__ void k_keys(const double *__restrict__ X, long long n, int d, const int *__restrict__ feat,
                        const int *__restrict__ dws, int P, int n_os, int B, int NB, int KB,
@@ -55,27 +55,107 @@ __global__ void k_radix_hist(const uint32_t *__restrict__ keys, long long cnt, i
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * nblk + blockIdx.x] = h[i];
 }
 
-// exclusive scan of len ints in place, one block of 1024 threads
-__global__ void k_scan_exclusive(int *data, long long len) {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const long long per = (len + 1023) / 1024;
-    const long long a = t * per, b = min(len, a + per);
-    long long s = 0;
-    for (long long i = a; i < b; ++i) s += data[i];
-    part[t] = s;
+// exclusive scan of len ints in place over tiles of kScanTile, two launches: per-tile sums, then
+// every tile scans itself after adding the sums of the tiles before it (at most a few hundred)
+constexpr int kScanTile = 8192;   // 1024 threads x 8 consecutive ints
+
+__device__ __forceinline__ int block_sum_1024(int v, int *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        long long v = t >= off ? part[t - off] : 0;
+    int s = lane < 32 ? red[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(const int *__restrict__ data, long long len,
+                                                         int *__restrict__ tsum) {
+    __shared__ int red[32];
+    const long long b0 = (long long)blockIdx.x * kScanTile;
+    int s = 0;
+    for (int k = 0; k < 8; ++k) {
+        const long long i = b0 + threadIdx.x + 1024LL * k;  // coalesced
+        if (i < len) s += data[i];
+    }
+    s = block_sum_1024(s, red);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = s;
+}
+
+// exclusive scan of the tile sums in place: one block, 1024 at a time with a running carry
+__global__ void __launch_bounds__(1024) k_scan_tile_prefix(int *__restrict__ tsum, int cnt) {
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry_s = 0;
+    __syncthreads();
+    for (int b = 0; b < cnt; b += 1024) {
+        const int own = b + t < cnt ? tsum[b + t] : 0;
+        int inc = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        part[t] += v;
+        if (warp == 0) {
+            int w = wsum[lane], wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        if (b + t < cnt) tsum[b + t] = carry + wsum[warp] + inc - own;
+        __syncthreads();
+        if (t == 1023) carry_s = carry + wsum[warp] + inc;
         __syncthreads();
     }
-    long long run = t == 0 ? 0 : part[t - 1];
-    for (long long i = a; i < b; ++i) {
-        const int x = data[i];
-        data[i] = (int)run;
-        run += x;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int *__restrict__ data, long long len,
+                                                     const int *__restrict__ tprefix) {
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int carry = tprefix[blockIdx.x];  // sum of all earlier tiles
+    const long long i0 = (long long)blockIdx.x * kScanTile + 8LL * t;
+    int v[8];
+    int own = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = i0 + k < len ? data[i0 + k] : 0;
+        own += v[k];
+    }
+    // exclusive scan of the per-thread sums: within the warp, then across warps
+    int inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = carry + wsum[warp] + inc - own;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (i0 + k < len) data[i0 + k] = run;
+        run += v[k];
     }
 }
 
@@ -382,12 +462,17 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         ANOVA_CUDA_TRY(cudaGetLastError());
     }
     const int nblk = (int)((total + kSortTile - 1) / kSortTile);
-    ANOVA_CUDA_TRY(cudaMalloc(&dhist.p, sizeof(int) * 256 * (size_t)nblk));
+    const long long hlen = 256LL * nblk;
+    const int nscan = (int)((hlen + kScanTile - 1) / kScanTile);
+    ANOVA_CUDA_TRY(cudaMalloc(&dhist.p, sizeof(int) * ((size_t)hlen + nscan)));
+    int *dtsum = (int *)dhist.p + hlen;
     uint32_t *kin = (uint32_t *)dk0.p, *kout = (uint32_t *)dk1.p;
     int *vin = (int *)dv0.p, *vout = (int *)dv1.p;
     for (int shift = 0; shift < keybits; shift += 8) {
         k_radix_hist<<<nblk, 256, 0, st>>>(kin, total, shift, (int *)dhist.p, nblk);
-        k_scan_exclusive<<<1, 1024, 0, st>>>((int *)dhist.p, 256LL * nblk);
+        k_scan_tile_sums<<<nscan, 1024, 0, st>>>((const int *)dhist.p, hlen, dtsum);
+        k_scan_tile_prefix<<<1, 1024, 0, st>>>(dtsum, nscan);
+        k_scan_tiles<<<nscan, 1024, 0, st>>>((int *)dhist.p, hlen, dtsum);
         k_radix_scatter<<<nblk, 32, 0, st>>>(kin, vin, kout, vout, total, shift, (const int *)dhist.p, nblk);
         ANOVA_CUDA_TRY(cudaGetLastError());
         std::swap(kin, kout);
@@ -690,8 +775,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     }
     if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
-    if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * 64)) != ANOVA_OK) return s;
-    ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * 64, st));
+    if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * kStatusAlloc)) != ANOVA_OK) return s;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * kStatusAlloc, st));
     for (int k = 0; k < 3; ++k) {
         ANOVA_CUDA_TRY(cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
         ANOVA_CUDA_TRY(cudaEventCreateWithFlags(&p->join_evt[k], cudaEventDisableTiming));

@@ -26,7 +26,12 @@ struct Request {
     int64_t footprint = 0;
     clock_type::time_point submitted;
     bool done = false;
+    int passed = 0;  // younger requests started ahead of this one while it did not fit
 };
+
+// A queued request that does not fit the budget may be passed by at most this many younger
+// requests that do fit; after that nothing younger starts until it has started.
+constexpr int kMaxPass = 4;
 
 }  // namespace
 
@@ -42,7 +47,7 @@ struct svm_server {
     std::vector<std::thread> workers;
     bool stopping = false;
     int64_t next_ticket = 1, submitted = 0, completed = 0, running = 0;
-    int64_t reserved = 0, peak_reserved = 0;
+    int64_t reserved = 0, peak_reserved = 0, backfilled = 0;
     std::vector<double> latencies_ms;
 };
 
@@ -90,16 +95,37 @@ static void worker_loop(svm_server *s) {
         Request *req = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            // admit the oldest request once it fits the budget (or nothing else is running)
+            // admission: the oldest request once it fits the budget (or nothing else is running);
+            // while it does not fit, the oldest younger request that fits may start instead
+            // (backfill), at most kMaxPass times past the same oldest request
+            auto chosen = s->queue.end();
+            auto pick = [&]() {
+                chosen = s->queue.end();
+                if (s->queue.empty()) return;
+                Request *head = s->queue.front();
+                if (s->reserved + head->footprint <= s->budget || s->running == 0) {
+                    chosen = s->queue.begin();
+                    return;
+                }
+                if (head->passed >= kMaxPass) return;
+                for (auto it = s->queue.begin() + 1; it != s->queue.end(); ++it)
+                    if (s->reserved + (*it)->footprint <= s->budget) {
+                        chosen = it;
+                        return;
+                    }
+            };
             s->cv_work.wait(lk, [&] {
                 if (s->stopping && s->queue.empty()) return true;
-                if (s->queue.empty()) return false;
-                const int64_t f = s->queue.front()->footprint;
-                return s->reserved + f <= s->budget || s->running == 0;
+                pick();
+                return chosen != s->queue.end();
             });
             if (s->queue.empty()) break;
-            req = s->queue.front();
-            s->queue.pop_front();
+            req = *chosen;
+            if (chosen != s->queue.begin()) {
+                s->queue.front()->passed += 1;
+                s->backfilled += 1;
+            }
+            s->queue.erase(chosen);
             s->running += 1;
             s->reserved += req->footprint;
             s->peak_reserved = std::max(s->peak_reserved, s->reserved);
@@ -221,6 +247,7 @@ anova_status svm_server_get_stats(svm_server_t s, svm_server_stats *out) {
     out->queued = (int64_t)s->queue.size();
     out->reserved_bytes = s->reserved;
     out->peak_reserved_bytes = s->peak_reserved;
+    out->backfilled = s->backfilled;
     if (!s->latencies_ms.empty()) {
         std::vector<double> v = s->latencies_ms;
         std::sort(v.begin(), v.end());

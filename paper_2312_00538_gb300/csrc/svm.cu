@@ -783,6 +783,27 @@ anova_status lowrank_factor(lowrank_t lr, double *L) {
     return ANOVA_OK;
 }
 
+anova_status lowrank_set_core_path(lowrank_t lr, int path) {
+    if (!lr) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    if (path != LOWRANK_CORE_AUTO && path != LOWRANK_CORE_SIMT && path != LOWRANK_CORE_TENSOR)
+        return fail(ANOVA_ERR_INVALID_ARG, "unknown core path");
+    if (path == LOWRANK_CORE_TENSOR && !core_tc_supported(lr))
+        return fail(ANOVA_ERR_INVALID_ARG, "tensor-core Woodbury core needs rank <= 256");
+    lr->core_path = path;
+    return ANOVA_OK;
+}
+
+anova_status lowrank_core(lowrank_t lr, double *M, int *path_used) {
+    if (!lr) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    if (!lr->core_ready) return fail(ANOVA_ERR_INVALID_ARG, "call lowrank_precond_set_theta first");
+    cudaStream_t st = lr->plan->stream;
+    if (M)
+        ANOVA_CUDA_TRY(cudaMemcpyAsync(M, lr->Mcore, sizeof(double) * lr->rank * lr->rank, cudaMemcpyDeviceToDevice, st));
+    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (path_used) *path_used = lr->core_used;
+    return ANOVA_OK;
+}
+
 anova_status lowrank_precond_set_theta(lowrank_t lr, const double *theta, const double *y) {
     if (!lr || !theta || !y) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
     return lowrank_set_theta_impl(lr, theta, y);

@@ -8,7 +8,7 @@ available here: the dimensions d (6-12) and window counts P (2-4) lie in the pap
 (d 8-28, P 3-10) and n reaches its "large" regime (n > 1e5).
 """
 from .data import (SEED_BASE, minmax_scale, consecutive_windows, config1, config2, config3,
-                   config4, matvec_vectors, subsample_rows, small_problem, C_GRID, SIGMA_GRID)
+                   config4, config5, matvec_vectors, subsample_rows, small_problem, C_GRID, SIGMA_GRID)
 
 __all__ = ["SEED_BASE", "minmax_scale", "consecutive_windows", "config1", "config2", "config3",
-           "config4", "matvec_vectors", "subsample_rows", "small_problem", "C_GRID", "SIGMA_GRID"]
+           "config4", "config5", "matvec_vectors", "subsample_rows", "small_problem", "C_GRID", "SIGMA_GRID"]

@@ -137,3 +137,32 @@ def config4(count=64, n_lo=5_000, n_hi=200_000, seed=None, d=9):
         probs.append(dict(X=minmax_scale(Xr), y=y, windows=consecutive_windows(d),
                           C=C_GRID[g // 4], sigma=SIGMA_GRID[g % 4]))
     return probs
+
+
+def config5(count, rate, seed=None, n_lo=10_000, n_hi=500_000):
+    """Workload 5 (serving): `count` SVM solve requests arriving as a Poisson stream of `rate`
+    requests per second. Request i: n log-uniform in [n_lo, n_hi], d uniform in {6, 9, 12, 15, 18}
+    (consecutive 3-D windows), (C, sigma) drawn from the grid of workload 4, 8 of every 12 features
+    N(0,1) and the rest Bernoulli(1/2) as in workload 3, labels from the tanh teacher with 5 % flips.
+    Returns a list of dicts with keys X, y, windows, C, sigma and arrival (seconds from the start)."""
+    rng = np.random.default_rng(SEED_BASE + 5 if seed is None else seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), size=count)).astype(np.int64)
+    ds = rng.choice([6, 9, 12, 15, 18], size=count)
+    grid = rng.integers(0, 16, size=count)
+    reqs = []
+    for i in range(count):
+        sub = np.random.default_rng(SEED_BASE + 5000 + i)
+        n, d = int(ns[i]), int(ds[i])
+        nb = d // 3
+        Xg = sub.standard_normal((n, d - nb))
+        Xb = sub.integers(0, 2, size=(n, nb)).astype(np.float64)
+        Xr = np.concatenate([Xg, Xb], axis=1)
+        y = _sign(_tanh_teacher(sub, Xr))
+        flip = sub.choice(n, size=int(round(0.05 * n)), replace=False)
+        y[flip] = -y[flip]
+        g = int(grid[i])
+        reqs.append(dict(X=minmax_scale(Xr), y=y, windows=consecutive_windows(d), C=C_GRID[g // 4],
+                         sigma=SIGMA_GRID[g % 4], arrival=float(arrivals[i])))
+    return reqs
+

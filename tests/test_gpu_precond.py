@@ -218,3 +218,44 @@ def test_woodbury_at_large_rank(env, rank):
     ref = op.blockdiag_apply(L32, theta, y, g, s)
     got = x.cpu().numpy()
     assert np.allclose(got, ref, rtol=1e-8, atol=1e-10 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n, rank", [(20000, 200), (6000, 100), (3000, 57), (700, 256)])
+def test_woodbury_core_on_tensor_cores_is_fp64_accurate(env, n, rank):
+    """M = I + L^T Theta^-1 L (Sec. 5) from exact bf16 slices on the tensor cores agrees with the
+    FP64 evaluation of the same sum (host, from the FP32 panel the library uses) to 1e-13 of its
+    norm, with Theta^-1 spread over 1e-2 .. 1e8 as late interior point steps produce it; so does the
+    FP64-pipe path. Both Cholesky factors then succeed and the applies agree."""
+    torch, ab = env
+    from synth import config3
+    cfg = config3(n=n)
+    plan = ab.anova_nfft_plan(cfg["X"], cfg["windows"], 1.0, N=64, m=6, flags=ab.ANOVA_FP64)
+    lr = ab.lowrank_precond_build(plan, ab.PCHOL_GREEDY, rank, 0.0)
+    L, _ = _factor(torch, ab, lr, n)
+    r = L.shape[1]
+    assert r == rank
+    L32 = L.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(rank)
+    itheta = 10.0 ** rng.uniform(-2, 8, n)
+    theta = 1.0 / itheta
+    ref = np.eye(r) + L32.T @ (itheta[:, None] * L32)
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    th, yy = dev(theta), dev(cfg["y"])
+    got = {}
+    for path in (ab.LOWRANK_CORE_SIMT, ab.LOWRANK_CORE_TENSOR):
+        ab.lowrank_set_core_path(lr, path)
+        for rep in range(2):                  # the second call reuses the slice workspace
+            ab.lowrank_precond_set_theta(lr, th, yy)
+            M = torch.empty((r, r), dtype=torch.float64, device="cuda")
+            assert ab.lowrank_core(lr, M) == path
+            got[(path, rep)] = M.cpu().numpy()
+    nrm = np.linalg.norm(ref)
+    for key, M in got.items():
+        assert np.linalg.norm(M - ref) <= 1e-13 * nrm, (key, np.linalg.norm(M - ref) / nrm)
+        assert np.array_equal(M, M.T)
+    # deterministic: the tensor-core path gives the same bits call after call
+    assert np.array_equal(got[(ab.LOWRANK_CORE_TENSOR, 0)], got[(ab.LOWRANK_CORE_TENSOR, 1)])
+    # the default path picks the tensor cores at this rank
+    ab.lowrank_set_core_path(lr, ab.LOWRANK_CORE_AUTO)
+    ab.lowrank_precond_set_theta(lr, th, yy)
+    assert ab.lowrank_core(lr) == ab.LOWRANK_CORE_TENSOR

@@ -76,3 +76,29 @@ def test_server_streaming_submission():
         alpha, b, _, status = _alone(ab, p, tol)
         assert r[3] == status == ab.ANOVA_OK
         assert np.array_equal(alpha, r[0]) and b == r[1]
+
+
+def test_server_backfills_a_request_that_fits_past_one_that_does_not():
+    """With A running and the budget too small for B beside it, C (younger, small) starts before B
+    instead of waiting behind it (backfill); every result is still the one alone."""
+    torch, ab = require_gpu()
+    from synth import small_problem
+    probs = [small_problem(1600, 9, 21), small_problem(1500, 9, 22), small_problem(300, 9, 23)]
+    tol = 1e-7
+    o = _opts(ab)
+    foot = [ab.svm_request_footprint(p["X"].shape[0], len(p["windows"]), o) for p in probs]
+    budget = foot[0] + foot[2]
+    assert foot[0] + foot[1] > budget
+    srv = ab.SvmServer(tol, opts=o, slots=2, hbm_budget_bytes=budget)
+    try:
+        tickets = [srv.submit(p["X"], p["y"], 1.0, windows=p["windows"]) for p in probs]
+        results = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["completed"] == 3 and st["backfilled"] >= 1
+    assert st["peak_reserved_bytes"] <= budget
+    for p, r in zip(probs, results):
+        alpha, b, _, status = ab.svm_ipm_solve(p["X"], p["y"], 1.0, tol, opts=o, windows=p["windows"])
+        assert r[3] == status == ab.ANOVA_OK
+        assert np.array_equal(alpha, r[0]) and b == r[1]
