@@ -311,6 +311,15 @@ anova_status anova_plan_check(anova_plan_t plan);
  */
 anova_status anova_plan_set_wait_limit(anova_plan_t plan, int64_t polls);
 
+/*
+ * anova_measure_fp32_peak -- measures the FP32 multiply-add rate of the current GPU in TFLOP/s
+ * (independent paired FMA chains on every SM, best of five CUDA-event-timed launches; a few
+ * milliseconds). It is the measured roofline denominator of the spread and interpolation kernels,
+ * which are bound by the FP32 pipe rather than by memory. The paper has no counterpart.
+ * Errors: INVALID_ARG (NULL), CUDA.
+ */
+anova_status anova_measure_fp32_peak(double *tflops);
+
 /* Release a plan and its device memory (NULL is ignored). Synchronises its stream. */
 void anova_plan_destroy(anova_plan_t plan);
 

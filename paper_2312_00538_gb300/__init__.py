@@ -82,6 +82,7 @@ _SIGNATURES = {
     "anova_plan_destroy": (None, [_vp]),
     "anova_plan_check": (_c_int, [_vp]),
     "anova_plan_set_wait_limit": (_c_int, [_vp, _c_i64]),
+    "anova_measure_fp32_peak": (_c_int, [_dp]),
     "anova_cross_matvec": (_c_int, [_vp, _vp, _vp, _vp]),
     "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
@@ -378,6 +379,13 @@ def anova_plan_check(plan):
 def anova_plan_set_wait_limit(plan, polls):
     """Polls of each tensor-core completion wait before it gives up (negative: the default)."""
     _check(lib().anova_plan_set_wait_limit(plan.handle, int(polls)))
+
+
+def anova_measure_fp32_peak():
+    """Measured FP32 multiply-add rate of the current GPU (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(lib().anova_measure_fp32_peak(ctypes.byref(v)))
+    return v.value
 
 
 def anova_plan_destroy(plan):

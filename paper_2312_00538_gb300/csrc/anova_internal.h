@@ -31,6 +31,8 @@ constexpr int kConvLines = ANOVA_CONV_LINES;  // grid lines per CTA of an FFT pa
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
+constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core
+                                          // interpolation (FP32, m = 4, 3-D windows)
 constexpr int kStatusAlloc = 128;      // ints of a plan's status/counter block (>= 1 + 3 x 32)
 
 // ----------------------------------------------------------------------------- host maths

@@ -13,8 +13,7 @@
 //   I_u = sum_{s + t = u} Q_s^T Q_t   (u < S; the terms with s + t >= S are below FP64 rounding).
 // Every product of two slices is an integer of magnitude <= 2^{2w} = 2^12, so a sum over 4096
 // rows is an integer below 2^24 and the FP32 accumulator holds it exactly. Each CTA therefore
-// accumulates one 4096-row chunk of the stacked products [Q_0 .. Q_u]^T [Q_u .. Q_0] on the
-// tensor cores (tcgen05.mma kind::f16, bf16 inputs, M = 128 rows a, N = 128 or 256 columns b,
+// accumulates Q_s^T Q_t over one block of 4096 rows on the tensor cores (tcgen05.mma kind::f16, bf16 inputs, M = 128 rows a, N = 128 or 256 columns b,
 // FP32 accumulator in tensor memory) and adds the exact chunk sums into FP64 accumulators of I_u
 // with atomics. The totals stay integers below 2^53, so FP64 addition is exact in any order and
 // the result does not depend on the order in which CTAs finish. A last kernel scales and sums the
@@ -35,7 +34,7 @@ namespace {
 
 constexpr int kW = 6;            // bits per slice
 constexpr int kS = 9;            // slices
-constexpr int kChunk = 4096;     // rows of the stacked products per exact FP32 accumulation
+constexpr int kChunk = 4096;     // rows per exact FP32 accumulation (one CTA)
 constexpr int kKS = 32;          // rows per shared-memory stage (two K = 16 products)
 constexpr int kNS = 4;           // stage slots (three stages in flight while one is multiplied)
 constexpr int kMRows = 128;      // MMA M: rows a per CTA
@@ -127,24 +126,29 @@ __global__ void __launch_bounds__(256) k_core_slice(const float *__restrict__ L,
 struct CoreMmaArgs {
     const __nv_bfloat16 *Q;  // [kS][RP][np]
     long long np;
-    int RP, r;
-    const int4 *work;        // per CTA: {u, chunk, row block, 0}
+    int r;
+    const int4 *work;        // per CTA: {s, t, row block, 0} with s <= t, s + t < kS
     double *I;               // [kS][RP][RP] integer accumulators (upper triangle, a <= b < r)
     int *status;             // bit 0: a bounded wait ran out
 };
 
-template <int N>
+// RP = 128 or 256 rows a (= columns b); the CTA holds all of them: RP / 128 accumulators of
+// 128 x RP in tensor memory (at most 512 columns)
+template <int RP>
 struct CoreCfg {
-    static constexpr uint32_t A_BYTES = kMRows * kKS * 2, B_BYTES = N * kKS * 2;
-    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr int MB = RP / kMRows;            // MMA row blocks
+    static constexpr uint32_t T_BYTES = RP * kKS * 2; // one operand tile (RP rows x kKS)
+    static constexpr uint32_t STAGE = 2 * T_BYTES;    // A (slice s) and B (slice t)
     static constexpr uint32_t MBAR = kNS * STAGE, SLOT = MBAR + 8 * kNS;
     static constexpr size_t smem = SLOT + 16;
+    static constexpr uint32_t TMEM_COLS = MB * RP;
     // bf16 operands, K-major, no swizzle: core matrices of 8 rows x 16 bytes (8 bf16);
-    // element (row, k) of a stage at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2
+    // element (row, k) of a tile at (row / 8) * SBO + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2
     static constexpr uint32_t LBO = 128, SBO = 128 * (kKS / 8);
     // kind::f16: FP32 accumulator (bit 4), A and B bf16 (bits 7, 10), K-major, N >> 3, M >> 4
-    static constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+    static constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RP >> 3) << 17) |
                                       ((uint32_t)(kMRows >> 4) << 24);
+    static_assert(TMEM_COLS <= 512, "accumulators fit the tensor memory of an SM");
 };
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -162,22 +166,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
-template <int N>
-__global__ void __launch_bounds__(128, 2) k_core_mma(CoreMmaArgs a) {
-    using C = CoreCfg<N>;
+// P = Q_s^T Q_t over rows k0 .. k0 + kChunk - 1 (exact in FP32), added to I_{s + t}: for s < t the
+// pair (t, s) gives P^T, so every entry P(a, b) goes to the upper-triangle slot (min, max), the
+// diagonal twice; for s = t, P is symmetric and only its upper triangle is added.
+template <int RP>
+__global__ void __launch_bounds__(128, 1) k_core_mma(CoreMmaArgs a) {
+    using C = CoreCfg<RP>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + C::MBAR);
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem_raw + C::SLOT);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int4 wk = a.work[blockIdx.x];
-    const int u = wk.x, chunk = wk.y, rb = wk.z;
-    const long long Kt = (long long)(u + 1) * a.np;           // rows of the stacked products
-    const long long k0 = (long long)chunk * kChunk;
-    const int nst = (int)((min(Kt, k0 + kChunk) - k0) / kKS);  // np is a multiple of kKS
+    const int s_a = wk.x, s_b = wk.y, u = wk.x + wk.y;
+    const bool same = s_a == s_b;                               // A tile = B tile
+    const long long k0 = (long long)wk.z * kChunk;
+    const int nst = (int)((min(a.np, k0 + kChunk) - k0) / kKS);  // np is a multiple of kKS
 
-    if (warp == 0) tc::tmem_alloc(slot, N);
+    if (warp == 0) tc::tmem_alloc(slot, C::TMEM_COLS);
     if (t == 0) {
-        for (int s = 0; s < kNS; ++s) tc::mbar_init(&mbar[s], 1);
+        for (int q = 0; q < kNS; ++q) tc::mbar_init(&mbar[q], 1);
         tc::mbar_init_fence();
     }
     tc::fence_before_sync();
@@ -186,25 +193,19 @@ __global__ void __launch_bounds__(128, 2) k_core_mma(CoreMmaArgs a) {
     const uint32_t tmem = *slot;
     const uint32_t sbase = tc::smem_u32(smem_raw);
 
-    // stage j: rows k0 + kKS j .. of the stacked products; A rows come from slice s, B rows from
-    // slice u - s (a stage never straddles two slices: np is a multiple of kKS)
+    // stage j: rows k0 + kKS j .. of slice s_b (B tile) and, unless s_a = s_b, of slice s_a (A tile)
     auto load_stage = [&](int j, int sl) {
-        const long long kk = k0 + (long long)j * kKS;
-        const int s = (int)(kk / a.np);
-        const long long ki = kk - (long long)s * a.np;
-        const __nv_bfloat16 *qa = a.Q + ((long long)s * a.RP + rb * kMRows) * a.np + ki;
-        const __nv_bfloat16 *qb = a.Q + ((long long)(u - s) * a.RP) * a.np + ki;
-        const uint32_t sa = sbase + sl * C::STAGE, sb = sa + C::A_BYTES;
-        // 16-byte pieces: row = idx / PC, piece = idx % PC (8 bf16 along k)
-        constexpr int PC = kKS / 8;
-        for (int idx = t; idx < (kMRows + N) * PC; idx += 128) {
-            const int row = idx / PC, pc = idx % PC;
-            if (row < kMRows)
-                cp_async16(sa + (row >> 3) * C::SBO + pc * C::LBO + (row & 7) * 16, qa + (long long)row * a.np + pc * 8);
-            else {
-                const int br = row - kMRows;
-                cp_async16(sb + (br >> 3) * C::SBO + pc * C::LBO + (br & 7) * 16, qb + (long long)br * a.np + pc * 8);
-            }
+        const long long ki = k0 + (long long)j * kKS;
+        const __nv_bfloat16 *qb = a.Q + (long long)s_b * RP * a.np + ki;
+        const __nv_bfloat16 *qa = a.Q + (long long)s_a * RP * a.np + ki;
+        const uint32_t sb = sbase + sl * C::STAGE, sa = sb + C::T_BYTES;
+        constexpr int PC = kKS / 8;  // 16-byte pieces per row
+        const int pieces = (same ? 1 : 2) * RP * PC;
+        for (int idx = t; idx < pieces; idx += 128) {
+            const int tile = idx / (RP * PC), e = idx % (RP * PC);
+            const int row = e / PC, pc = e % PC;
+            const uint32_t off = (row >> 3) * C::SBO + pc * C::LBO + (row & 7) * 16;
+            cp_async16((tile ? sa : sb) + off, (tile ? qa : qb) + (long long)row * a.np + pc * 8);
         }
     };
 
@@ -222,12 +223,15 @@ __global__ void __launch_bounds__(128, 2) k_core_mma(CoreMmaArgs a) {
         if (__syncthreads_or(failed)) break;
         if (t == 0) {
             tc::fence_after_sync();
-            const uint32_t sa = sbase + sl * C::STAGE, sb = sa + C::A_BYTES;
+            const uint32_t sb = sbase + sl * C::STAGE, sa = same ? sb : sb + C::T_BYTES;
 #pragma unroll
             for (int ks = 0; ks < kKS / 16; ++ks) {
-                const uint64_t ad = tc::smem_desc(sa + ks * 256, C::LBO, C::SBO);
                 const uint64_t bd = tc::smem_desc(sb + ks * 256, C::LBO, C::SBO);
-                mma_bf16(tmem, ad, bd, C::idesc, it > 0 || ks > 0);
+#pragma unroll
+                for (int mb = 0; mb < C::MB; ++mb) {
+                    const uint64_t ad = tc::smem_desc(sa + mb * (kMRows / 8) * C::SBO + ks * 256, C::LBO, C::SBO);
+                    mma_bf16(tmem + (uint32_t)(mb * RP), ad, bd, C::idesc, it > 0 || ks > 0);
+                }
             }
             tc::mma_commit(&mbar[sl]);
         }
@@ -243,23 +247,32 @@ __global__ void __launch_bounds__(128, 2) k_core_mma(CoreMmaArgs a) {
         cp_async_commit();
     }
     cp_async_wait<0>();
-    // the last committed stage's barrier covers every product before the accumulator is read
+    // the last committed stage's barrier covers every product before the accumulators are read
     const bool ok = !__syncthreads_or(failed);
     bool done = last >= 0 && tc::mbar_wait_bounded(&mbar[last % kNS], (uint32_t)((last / kNS) & 1), kMaxPolls);
     done = __syncthreads_and(done && ok);
     if (done) {
         tc::fence_after_sync();
-        const int arow = rb * kMRows + warp * 32 + lane;
-        double *Iu = a.I + (long long)u * a.RP * a.RP + (long long)arow * a.RP;
+        double *Iu = a.I + (long long)u * RP * RP;
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (arow < a.r) {
+        for (int mb = 0; mb < C::MB; ++mb) {
+            const int arow = mb * kMRows + warp * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < RP; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mb * RP + c0), v);
+                if (arow < a.r) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int b = c0 + j;
-                    if (b >= arow && b < a.r && v[j] != 0.0f) atomicAdd(&Iu[b], (double)v[j]);
+                    for (int j = 0; j < 32; ++j) {
+                        const int b = c0 + j;
+                        if (b >= a.r || v[j] == 0.0f) continue;
+                        if (same) {
+                            if (b >= arow) atomicAdd(&Iu[(long long)arow * RP + b], (double)v[j]);
+                        } else {
+                            const int lo = min(arow, b), hi = max(arow, b);
+                            atomicAdd(&Iu[(long long)lo * RP + hi], (b == arow ? 2.0 : 1.0) * (double)v[j]);
+                        }
+                    }
                 }
             }
         }
@@ -268,7 +281,7 @@ __global__ void __launch_bounds__(128, 2) k_core_mma(CoreMmaArgs a) {
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, N);
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
 // M(a, b) = [a == b] + sum_{u = S-1 .. 0} 2^{E_a + E_b - w(u + 2)} I_u(a, b), symmetric, row-major.
@@ -299,13 +312,14 @@ static anova_status core_tc_prepare(lowrank *lr) {
     lr->tc_np = (n + kKS - 1) / kKS * kKS;
     lr->tc_RP = r <= 128 ? 128 : 256;
     const int RP = lr->tc_RP;
+    // one CTA per slice pair s <= t with s + t < kS (25 pairs; Q_t^T Q_s is the transpose of
+    // Q_s^T Q_t) and block of kChunk rows; the pairs of one row block are consecutive, so that CTAs
+    // running together share that block of every slice in L2
     std::vector<int4> work;
-    for (int u = 0; u < kS; ++u) {
-        const long long Kt = (long long)(u + 1) * lr->tc_np;
-        const int chunks = (int)((Kt + kChunk - 1) / kChunk);
-        for (int rb = 0; rb * kMRows < r; ++rb)
-            for (int c = 0; c < chunks; ++c) work.push_back(make_int4(u, c, rb, 0));
-    }
+    const int blocks = (int)((lr->tc_np + kChunk - 1) / kChunk);
+    for (int c = 0; c < blocks; ++c)
+        for (int sa = 0; sa < kS; ++sa)
+            for (int sb = sa; sa + sb < kS; ++sb) work.push_back(make_int4(sa, sb, c, 0));
     lr->tc_nwork = (int)work.size();
     cudaError_t e;
     if ((e = cudaMalloc(&lr->tc_Q, sizeof(__nv_bfloat16) * (size_t)kS * RP * lr->tc_np)) != cudaSuccess ||
@@ -344,7 +358,6 @@ anova_status core_tc(lowrank *lr) {
     CoreMmaArgs ma;
     ma.Q = (const __nv_bfloat16 *)lr->tc_Q;
     ma.np = lr->tc_np;
-    ma.RP = RP;
     ma.r = r;
     ma.work = (const int4 *)lr->tc_work;
     ma.I = lr->tc_I;

@@ -20,7 +20,6 @@ namespace anova {
 #ifndef ANOVA_GROUP_ORDER
 #define ANOVA_GROUP_ORDER 0   // largest-first order over a whole dimension group (else per window)
 #endif
-constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core form
 constexpr int kAuxStreams = 3;           // concurrent window chains of one matvec
 #ifndef ANOVA_INTERP_VARIANT
 // FP32 3-D interpolation with m = 4: 2 = tensor cores where chosen, 0 = always one point per lane

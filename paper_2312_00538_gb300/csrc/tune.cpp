@@ -21,6 +21,19 @@ struct Setting {
     int interp, rhs_chunk, fork;
 };
 
+// The interpolation form an FP32 plan with 3-D windows and m = 4 uses when neither form is forced
+// (the rule of the interpolation stage: tensor cores once work items are well filled).
+int auto_interp(const anova_plan *p) {
+    for (const Group &g : p->groups) {
+        if (g.dw != 3) continue;
+        const int wi0 = p->win[g.w_begin].wi_begin, wi1 = p->win[g.w_end - 1].wi_end;
+        return (double)p->n * (g.w_end - g.w_begin) >= (double)kTcMinPointsPerItem * (wi1 - wi0)
+                   ? ANOVA_INTERP_TENSOR
+                   : ANOVA_INTERP_SIMT;
+    }
+    return 0;
+}
+
 void apply(anova_plan *p, const Setting &s) {
     p->interp_flags = s.interp;
     p->rhs_chunk = s.rhs_chunk;
@@ -152,8 +165,11 @@ anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *wi
     Setting best_set = def;
     if ((s = search(best, &best_set, &best_ms)) != ANOVA_OK) return s;
     if (def_ms < best_ms) {
+        // the default setting is one of the searched ones (the automatic interpolation form is
+        // one of the two); it won within timing noise: keep it, stated with its resolved form
         best_ms = def_ms;
         best_set = def;
+        if (two_interp) best_set.interp = auto_interp(best);
     }
     // other work-item caps need their own plan tables
     for (int wi_max : {kWiMax / 2, kWiMax * 2}) {
