@@ -147,6 +147,29 @@ anova_status anova_conv_grid(anova_plan_t plan, int l, const void *grid_in, void
 anova_status anova_interp_grid(anova_plan_t plan, int l, const void *grid, void *f);
 
 /*
+ * Split matvec for a product whose points are split over several plans (row sharding, e.g. one
+ * plan per GPU). The inner sum of the fast summation (Sec. 3: the adjoint NFFT, a sum over the
+ * points) is additive over any partition of the points, so with the points split over plans
+ * built from the same windows, N, m, precision and per-window ell_l, eta_l:
+ *   (K v)[rows of plan k] = from_grids(plan k, sum over plans j of grids(plan j, v_j)).
+ * anova_plan_grid_size -- grid_total: values of one right-hand side's grids, every window's
+ *   n_os^{d_l} grid back to back (the same for all plans with the same windows and N).
+ * anova_matvec_grids -- the spread of v (device, n x nrhs column-major, the plan's points) into
+ *   every window's oversampled grid: grids (device, nrhs x grid_total, overwritten).
+ * anova_matvec_from_grids -- the rest of the product for the plan's points from summed grids
+ *   (device, nrhs x grid_total): every window's grid is convolved over the whole grid (FFT,
+ *   scaling, inverse FFT; a sum over several plans is not confined to this plan's box), then
+ *   interpolated at the plan's points and summed over windows into Kv (device, n x nrhs,
+ *   overwritten). With one plan, grids then from_grids equals anova_matvec up to the order of sums.
+ * Both run asynchronously on the plan's stream and use the plan's workspace (calls on one plan
+ * are ordered by the caller, as for anova_matvec). Errors: INVALID_ARG (NULL, nrhs < 1,
+ * overlapping buffers), OOM, CUDA.
+ */
+anova_status anova_plan_grid_size(anova_plan_t plan, int64_t *grid_total);
+anova_status anova_matvec_grids(anova_plan_t plan, const void *v, void *grids, int nrhs);
+anova_status anova_matvec_from_grids(anova_plan_t plan, const void *grids, void *Kv, int nrhs);
+
+/*
  * anova_spread_grid_noalloc -- anova_spread_grid (same kernels, same grid) without any device
  * allocation in the call. The paper has no counterpart; this exists for callers that cannot
  * allocate device memory when they call: processes whose device memory is entirely reserved

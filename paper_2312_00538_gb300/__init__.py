@@ -83,6 +83,9 @@ _SIGNATURES = {
     "anova_plan_check": (_c_int, [_vp]),
     "anova_plan_set_wait_limit": (_c_int, [_vp, _c_i64]),
     "anova_measure_fp32_peak": (_c_int, [_dp]),
+    "anova_plan_grid_size": (_c_int, [_vp, _lp]),
+    "anova_matvec_grids": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "anova_matvec_from_grids": (_c_int, [_vp, _vp, _vp, _c_int]),
     "anova_cross_matvec": (_c_int, [_vp, _vp, _vp, _vp]),
     "anova_plan_set_timing": (_c_int, [_vp, _c_int]),
     "anova_plan_stage_times": (_c_int, [_vp, _dp, _lp]),
@@ -379,6 +382,23 @@ def anova_plan_check(plan):
 def anova_plan_set_wait_limit(plan, polls):
     """Polls of each tensor-core completion wait before it gives up (negative: the default)."""
     _check(lib().anova_plan_set_wait_limit(plan.handle, int(polls)))
+
+
+def anova_plan_grid_size(plan):
+    """Values of one right-hand side's grids (every window's grid back to back)."""
+    g = ctypes.c_int64()
+    _check(lib().anova_plan_grid_size(plan.handle, ctypes.byref(g)))
+    return g.value
+
+
+def anova_matvec_grids(plan, v, grids, nrhs=1):
+    """Spread of v (device) into every window's grid (device, nrhs x grid_total)."""
+    _check(lib().anova_matvec_grids(plan.handle, _dev_ptr(v), _dev_ptr(grids), int(nrhs)))
+
+
+def anova_matvec_from_grids(plan, grids, Kv, nrhs=1):
+    """The product at the plan's points from (summed) grids (device) into Kv (device)."""
+    _check(lib().anova_matvec_from_grids(plan.handle, _dev_ptr(grids), _dev_ptr(Kv), int(nrhs)))
 
 
 def anova_measure_fp32_peak():

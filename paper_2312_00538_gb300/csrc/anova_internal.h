@@ -65,6 +65,7 @@ struct WindowInfo {
     int64_t grid_off = 0;            // element offset of this window's grid (one RHS)
     int bin_off = 0;                 // offset of this window's bin table
     int tile_begin[3] = {0, 0, 0}, tile_end[3] = {0, 0, 0};  // FFT tiles of each axis pass
+    int full_begin[3] = {0, 0, 0}, full_end[3] = {0, 0, 0};  // the same over the whole grid
     int mb_begin = 0, mb_end = 0;    // bins split into several work items
     int64_t box_volume() const {
         int64_t v = 1;
@@ -122,6 +123,7 @@ struct anova_plan {
     int4 *mbins = nullptr;        // multi-item bins: {first work item, count, tile volume, 0}
     int nmbins = 0;
     int4 *ftiles = nullptr;       // FFT tiles: {window, p, q0, pass}
+    int4 *ftiles_full = nullptr;  // FFT tiles over whole grids (products from summed grids)
     anova::DevWindow *dwin = nullptr;
     void *D1br = nullptr;         // T[P][3][n_os]: deconvolution diagonal per axis, bit-reversed
     void *tw = nullptr;           // T[n_os]: twiddles (re, im) pairs for k < n_os/2
@@ -193,6 +195,12 @@ template <typename T>
 anova_status run_interp_grid_t(anova_plan *p, int w, const void *grid, void *f);
 template <typename T>
 anova_status run_cross_matvec_t(anova_plan *src, anova_plan *tgt, const void *w, void *f);
+// Split matvec of a row-sharded product: the spread of v into every window's grid (grids:
+// nrhs x grid_total, overwritten), and the rest of the product from summed grids.
+template <typename T>
+anova_status run_matvec_grids_t(anova_plan *p, const void *v, void *grids, int nrhs);
+template <typename T>
+anova_status run_matvec_from_grids_t(anova_plan *p, const void *grids, void *Kv, int nrhs);
 // Source half into model->grid (allocated by the caller, grid_total elements); synchronises.
 template <typename T>
 anova_status run_model_create_t(anova_plan *src, const void *w, anova_model *model);

@@ -147,6 +147,42 @@ anova_status anova_matvec(anova_plan_t plan, const void *v, void *Kv, int nrhs) 
     });
 }
 
+anova_status anova_plan_grid_size(anova_plan_t plan, int64_t *grid_total) {
+    if (!plan || !grid_total) return fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    *grid_total = plan->grid_total;
+    return ANOVA_OK;
+}
+
+anova_status anova_matvec_grids(anova_plan_t plan, const void *v, void *grids, int nrhs) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!v || !grids) return fail(ANOVA_ERR_INVALID_ARG, "v or grids is NULL");
+        if (nrhs < 1) return fail(ANOVA_ERR_INVALID_ARG, "nrhs must be >= 1");
+        const size_t vb = elem_size(plan) * (size_t)plan->n * nrhs, gb = elem_size(plan) * (size_t)plan->grid_total * nrhs;
+        const char *a = (const char *)v, *b = (const char *)grids;
+        if (a < b + gb && b < a + vb) return fail(ANOVA_ERR_INVALID_ARG, "v and grids overlap");
+        DeviceGuard g(plan->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        if (plan->prec == ANOVA_FP64) return run_matvec_grids_t<double>(plan, v, grids, nrhs);
+        return run_matvec_grids_t<float>(plan, v, grids, nrhs);
+    });
+}
+
+anova_status anova_matvec_from_grids(anova_plan_t plan, const void *grids, void *Kv, int nrhs) {
+    return guarded([&]() -> anova_status {
+        if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");
+        if (!grids || !Kv) return fail(ANOVA_ERR_INVALID_ARG, "grids or Kv is NULL");
+        if (nrhs < 1) return fail(ANOVA_ERR_INVALID_ARG, "nrhs must be >= 1");
+        const size_t kb = elem_size(plan) * (size_t)plan->n * nrhs, gb = elem_size(plan) * (size_t)plan->grid_total * nrhs;
+        const char *a = (const char *)Kv, *b = (const char *)grids;
+        if (a < b + gb && b < a + kb) return fail(ANOVA_ERR_INVALID_ARG, "Kv and grids overlap");
+        DeviceGuard g(plan->device);
+        if (!g.ok) return fail(ANOVA_ERR_CUDA, "cannot select the plan's device");
+        if (plan->prec == ANOVA_FP64) return run_matvec_from_grids_t<double>(plan, grids, Kv, nrhs);
+        return run_matvec_from_grids_t<float>(plan, grids, Kv, nrhs);
+    });
+}
+
 anova_status anova_matvec_host(anova_plan_t plan, const void *v_host, void *Kv_host, int nrhs) {
     return guarded([&]() -> anova_status {
         if (!plan) return fail(ANOVA_ERR_INVALID_ARG, "plan is NULL");

@@ -311,6 +311,8 @@ WinParams make_winparams(const anova_plan *p) {
     WinParams wp{};
     for (int j = 0; j < 2 * p->m && j < 16; ++j)
         for (int q = 0; q <= kPolyDeg; ++q) wp.c[j][q] = (float)p->poly[(size_t)j * (kPolyDeg + 1) + q];
+    for (int j = 0; j < 2 * p->m && j < 8; ++j)
+        for (int q = 0; q <= kPolyDeg; ++q) wp.c2[j][q] = make_float2(wp.c[j][q], wp.c[j][q]);
     for (int j = 0; j < p->m && j < 8; ++j)
         for (int q = 0; q <= kPolyDeg64; ++q) wp.c64[j][q] = p->poly64[(size_t)j * (kPolyDeg64 + 1) + q];
     wp.beta = kb_beta();
@@ -599,6 +601,98 @@ anova_status matvec_impl(anova_plan *p, const T *v, T *Kv, int nrhs, int only_wi
         ANOVA_CUDA_TRY(launch_window_sum<T>(part, kr, p->n, nr, p->P, p->stream));
         p->launches += 1;
         stage_record(p, STAGE_SUM, e0, stage_event(p));
+    }
+    return ANOVA_OK;
+}
+
+}  // namespace anova
+
+namespace anova {
+
+// Split matvec, first half: the spread (and tile reduction) of v onto every window's grid, for all
+// nrhs columns, into grids[r][grid_total] (cleared first: the reduction writes only the box of
+// this plan's footprints).
+template <typename T>
+anova_status grids_impl(anova_plan *p, const T *v, T *grids, int nrhs) {
+    const int chunk = std::min(nrhs, std::max(1, std::min(16, p->rhs_chunk)));
+    anova_status st = ensure_workspace(p, chunk);
+    if (st != ANOVA_OK) return st;
+    const long long gs = p->grid_total;
+    ANOVA_CUDA_TRY(cudaMemsetAsync(grids, 0, sizeof(T) * (size_t)gs * nrhs, p->stream));
+    const WinParams wp = make_winparams<T>(p);
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+        const int nr = std::min(chunk, nrhs - r0);
+        for (const Group &gr : p->groups) {
+            const int wi0 = p->win[gr.w_begin].wi_begin, wi1 = p->win[gr.w_end - 1].wi_end;
+            SpreadArgs sa;
+            sa.packed = packed_path((int)sizeof(T), gr.dw, p->m) ? 1 : 0;
+            sa.wis = p->wis;
+            sa.segs = p->segs;
+            sa.frac = p->frac;
+            sa.perm = p->perm;
+            sa.v = v + (size_t)r0 * p->n;
+            sa.tiles = p->tiles;
+            sa.n = p->n;
+            sa.total = p->n * p->P;
+            sa.nrhs = nr;
+            sa.wi_begin = wi0;
+            sa.wi_end = wi1;
+            sa.wp = wp;
+            sa.order = ANOVA_SPREAD_ORDER ? p->wi_order : nullptr;
+            if (wi1 > wi0) {
+                cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nr, p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+                p->launches += 1;
+            }
+            st = launch_reduce<T>(p, gr.dw, gr.w_begin, gr.w_end, grids + (size_t)r0 * gs, gs, nr, 0, p->stream);
+            if (st != ANOVA_OK) return st;
+        }
+    }
+    return ANOVA_OK;
+}
+
+// Split matvec, second half: every window's grid of `grids` convolved over the whole grid (FFT,
+// scaling, inverse FFT: the summed grid is not confined to this plan's box), interpolated at the
+// plan's points and summed over windows into Kv.
+template <typename T>
+anova_status from_grids_impl(anova_plan *p, const T *grids, T *Kv, int nrhs) {
+    const int chunk = std::min(nrhs, std::max(1, std::min(16, p->rhs_chunk)));
+    anova_status st = ensure_workspace(p, chunk);
+    if (st != ANOVA_OK) return st;
+    const long long gs = p->grid_total;
+    T *ws = reinterpret_cast<T *>(p->grids);
+    T *g[4];
+    for (int k = 0; k < 4; ++k) g[k] = ws + (size_t)k * p->ws_rhs * gs;
+    T *part = reinterpret_cast<T *>(p->part);
+    const WinParams wp = make_winparams<T>(p);
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+        const int nr = std::min(chunk, nrhs - r0);
+        for (const Group &gr : p->groups) {
+            for (int pass = 0; pass < gr.dw; ++pass) {
+                ConvArgs ca;
+                ca.tiles = p->ftiles_full;
+                ca.in = pass == 0 ? (const void *)(grids + (size_t)r0 * gs) : (const void *)g[pass];
+                ca.out = pass == gr.dw - 1 ? g[3] : g[pass + 1];
+                ca.D1br = p->D1br;
+                ca.tw = p->tw;
+                ca.dwin = p->dwin;
+                ca.grid_stride_rhs = gs;
+                ca.tile_begin = p->win[gr.w_begin].full_begin[pass];
+                ca.tile_end = p->win[gr.w_end - 1].full_end[pass];
+                ca.zero_offset = 0;
+                const int nt = ca.tile_end - ca.tile_begin;
+                if (nt > 0) {
+                    cudaError_t e = dispatch_conv<T>(p->n_os, gr.dw, ca, nt, nr, p->stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "conv launch");
+                    p->launches += 1;
+                }
+            }
+            st = interp_stage<T>(p, gr, gr.w_begin, gr.w_end, 0, g[3], gs, nr, part, wp, p->stream,
+                                 p->dev_status + 1);
+            if (st != ANOVA_OK) return st;
+        }
+        ANOVA_CUDA_TRY(launch_window_sum<T>(part, Kv + (size_t)r0 * p->n, p->n, nr, p->P, p->stream));
+        p->launches += 1;
     }
     return ANOVA_OK;
 }

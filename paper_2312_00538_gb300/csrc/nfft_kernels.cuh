@@ -23,6 +23,12 @@
 #ifndef ANOVA_SPREAD_MINB
 #define ANOVA_SPREAD_MINB 3  // resident CTAs per SM the packed FP32 spread is compiled for
 #endif
+#ifndef ANOVA_WEIGHTS_PAIR
+#define ANOVA_WEIGHTS_PAIR 0  // x and y window weights with paired FMAs (same values)
+#endif
+#ifndef ANOVA_EPI_PAIR
+#define ANOVA_EPI_PAIR 0  // tensor-core interpolation: b-sums of the epilogue with paired FMAs
+#endif
 #ifndef ANOVA_SPREAD_UNROLL
 #define ANOVA_SPREAD_UNROLL 8  // points per unrolled group of the packed FP32 spread's inner loop
 #endif
@@ -408,8 +414,12 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
             // stage the current batch's weights (zeros for lanes past the batch)
             {
                 float wx[W2], wy[W2], wz[W2];
+#if ANOVA_WEIGHTS_PAIR
+                weights_pair<M>(fx, fy, a.wp, wx, wy);
+#else
                 Weights<float, M>::eval(fx, a.wp, wx);
                 Weights<float, M>::eval(fy, a.wp, wy);
+#endif
                 Weights<float, M>::eval(fz, a.wp, wz);
                 const float vl = lane < cnt ? vv : 0.0f;
 #pragma unroll
@@ -1126,8 +1136,12 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
         // on failures at the next barrier.
         auto finish = [&](int bf, const Chunk &ch, const Raw &rw) {
             float wx[W2], wy[W2];
+#if ANOVA_WEIGHTS_PAIR
+            weights_pair<M>(rw.f[0], rw.f[1], a.wp, wx, wy);
+#else
             Weights<float, M>::eval(rw.f[0], a.wp, wx);
             Weights<float, M>::eval(rw.f[1], a.wp, wy);
+#endif
             if (!tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, PARAM_WAIT ? a.wait_polls : C::kMaxPolls)) {
                 failed = true;
                 return;
@@ -1143,9 +1157,18 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                 tc::tmem_ld16(col + (uint32_t)(16 * q4), h);
 #pragma unroll
                 for (int aa = 0; aa < 2; ++aa) {
+#if ANOVA_EPI_PAIR
+                    // b-sums in pairs (even and odd b), the two halves added at the end
+                    f32x2 sp = zero2();
+#pragma unroll
+                    for (int b2 = 0; b2 < W2; b2 += 2)
+                        sp = fma2(make_float2(wy[b2], wy[b2 + 1]), make_float2(h[aa * W2 + b2], h[aa * W2 + b2 + 1]), sp);
+                    const float sb = sp.x + sp.y;
+#else
                     float sb = 0.0f;
 #pragma unroll
                     for (int b2 = 0; b2 < W2; ++b2) sb = fmaf(wy[b2], h[aa * W2 + b2], sb);
+#endif
                     f = fmaf(wx[2 * q4 + aa], sb, f);
                 }
             }

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <thread>
 
 #include "anova_internal.h"
 
@@ -253,6 +254,32 @@ struct DevBuf {
     }
 };
 
+// f(t, nt) on nt host threads (t = 0 .. nt - 1; the calling thread runs t = 0); nt is capped by the
+// hardware threads and by `items`, so small inputs stay on one thread
+template <typename F>
+void parallel_for_threads(long long items, long long min_per_thread, F f) {
+    const long long hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::max(1LL, std::min({hw, 16LL, items / std::max(1LL, min_per_thread)}));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(f, t, nt);
+    f(0, nt);
+    for (auto &x : th) x.join();
+}
+
+// cell index inside its bin of every sorted point: the low digits of its sort key
+__global__ void k_cellloc(const uint32_t *__restrict__ keys, long long total, int KB, int B,
+                          const int *__restrict__ dws, unsigned char *__restrict__ loc) {
+    const uint32_t kmask = KB >= 32 ? 0xffffffffu : ((1u << KB) - 1u);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[q];
+        const int w = (int)(key >> KB);
+        uint32_t bvol = 1;
+        for (int k = 0; k < dws[w]; ++k) bvol *= (uint32_t)B;
+        loc[q] = (unsigned char)((key & kmask) % bvol);
+    }
+}
+
 }  // namespace
 
 size_t elem_size(const anova_plan *p) { return p->prec == ANOVA_FP64 ? sizeof(double) : sizeof(float); }
@@ -306,7 +333,7 @@ void destroy_plan(anova_plan *p) {
     }
     if (p->fork_evt) cudaEventDestroy(p->fork_evt);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -364,13 +391,21 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         for (int l = 0; l < P; ++l)
             for (int k = 0; k < 3; ++k)
                 if (windows[3 * l + k] >= 0) used[windows[3 * l + k]] = 1;
-        for (int64_t i = 0; i < n; ++i)
-            for (int k = 0; k < d; ++k) {
-                const double x = points[i * d + k];
-                if (!std::isfinite(x)) return fail(ANOVA_ERR_NONFINITE, "points hold NaN or Inf");
-                if (used[k] && (x < -kBoxHalf - 1e-12 || x > kBoxHalf + 1e-12))
-                    return fail(ANOVA_ERR_OUT_OF_RANGE, "a point coordinate lies outside [-0.2, 0.2]");
-            }
+        // rows split over host threads; each records the kind of the first bad value it meets
+        std::vector<int> bad(16, 0);  // 1: not finite, 2: outside the box
+        parallel_for_threads(n, 1 << 16, [&](int t, int nt) {
+            const int64_t i0 = n * t / nt, i1 = n * (t + 1) / nt;
+            for (int64_t i = i0; i < i1 && !bad[t]; ++i)
+                for (int k = 0; k < d; ++k) {
+                    const double x = points[i * d + k];
+                    if (!std::isfinite(x)) { bad[t] = 1; break; }
+                    if (used[k] && (x < -kBoxHalf - 1e-12 || x > kBoxHalf + 1e-12)) { bad[t] = 2; break; }
+                }
+        });
+        for (int b : bad) {
+            if (b == 1) return fail(ANOVA_ERR_NONFINITE, "points hold NaN or Inf");
+            if (b == 2) return fail(ANOVA_ERR_OUT_OF_RANGE, "a point coordinate lies outside [-0.2, 0.2]");
+        }
     }
     std::unique_ptr<anova_plan, void (*)(anova_plan *)> plan(new (std::nothrow) anova_plan(),
                                                             destroy_plan);
@@ -420,10 +455,21 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     const int lb = ilog2(nos);
     // deconvolution diagonal per window and axis, bit-reversed; eta_l scales the axis-0 copy
     std::vector<double> d1br((size_t)P * 3 * nos, 0.0);
+    std::vector<std::pair<double, std::vector<double>>> d1_cache;  // windows with the same ell share it
     for (int w = 0; w < P; ++w) {
         std::vector<double> D1;
-        if (!deconv_diag(p->win[w].ell, N, m, nos, D1))
-            return fail(ANOVA_ERR_INVALID_ARG, "kernel coefficient fit failed");
+        bool cached = false;
+        for (auto &c : d1_cache)
+            if (c.first == p->win[w].ell) {
+                D1 = c.second;
+                cached = true;
+                break;
+            }
+        if (!cached) {
+            if (!deconv_diag(p->win[w].ell, N, m, nos, D1))
+                return fail(ANOVA_ERR_INVALID_ARG, "kernel coefficient fit failed");
+            d1_cache.emplace_back(p->win[w].ell, D1);
+        }
         for (int ax = 0; ax < 3; ++ax)
             for (int e = 0; e < nos; ++e)
                 d1br[((size_t)w * 3 + ax) * nos + e] = D1[bitrev(e, lb)] * (ax == 0 ? p->win[w].eta : 1.0);
@@ -518,15 +564,21 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         }
         p->groups.back().w_end = w + 1;
     }
-    for (int w = 0; w < P; ++w) {
+    // per-window tables built on host threads (windows are independent), then concatenated
+    struct WinTables {
+        std::vector<int4> segs, wis;  // segment indices relative to the window's first segment
+        std::vector<int2> bins;       // work-item indices relative to the window's first work item
+        int cmin[3] = {0, 0, 0}, cmax[3] = {-1, -1, -1};
+        bool bad = false;             // a bin tile would leave the grid (N too small for m)
+    };
+    std::vector<WinTables> wt(P);
+    auto build_window = [&](int w) {
         WindowInfo &wi = p->win[w];
+        WinTables &o = wt[w];
         const int dw = wi.dw;
         int bvol = 1, nbins = 1;
         for (int k = 0; k < dw; ++k) { bvol *= B; nbins *= NB; }
-        wi.seg_begin = (int)segs.size();
-        wi.wi_begin = (int)wis.size();
-        wi.bin_off = (int)bins.size();
-        bins.resize(bins.size() + nbins, make_int2(0, 0));
+        o.bins.assign(nbins, make_int2(0, 0));
         int cmin[3] = {nos, nos, nos}, cmax[3] = {-1, -1, -1};
         const long long q0 = (long long)w * n, q1 = q0 + n;
         uint32_t prev = 0xffffffffu;
@@ -534,7 +586,7 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         for (long long q = q0; q < q1; ++q) {
             const uint32_t key = hkeys[q] & kmask;
             const bool new_cell = key != prev;
-            if (new_cell || segs.back().z >= kSegMax) {
+            if (new_cell || o.segs.back().z >= kSegMax) {
                 const uint32_t bin = key / bvol, loc = key % bvol;
                 int c[3] = {0, 0, 0};
                 uint32_t bb = bin, ll = loc;
@@ -548,38 +600,55 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     cmax[k] = std::max(cmax[k], c[k]);
                 }
                 const int packed = c[0] | (c[1] << 10) | (c[2] << 20);
-                segs.push_back(make_int4(packed, (int)q, 0, w));
+                o.segs.push_back(make_int4(packed, (int)q, 0, w));
                 // work items: runs of one bin's segments, at most wi_max points
                 if ((int)bin != cur_bin || wi_pts + kSegMax > p->wi_max) {
                     int bc[3] = {0, 0, 0};
                     uint32_t b2 = bin;
                     for (int k = dw - 1; k >= 0; --k) { bc[k] = (int)(b2 % NB); b2 /= NB; }
-                    wis.push_back(make_int4(w, (int)segs.size() - 1, (int)segs.size(),
-                                            bc[0] | (bc[1] << 10) | (bc[2] << 20)));
+                    o.wis.push_back(make_int4(w, (int)o.segs.size() - 1, (int)o.segs.size(),
+                                              bc[0] | (bc[1] << 10) | (bc[2] << 20)));
                     if ((int)bin != cur_bin) {
-                        bins[wi.bin_off + bin] = make_int2((int)wis.size() - 1, 0);
+                        o.bins[bin] = make_int2((int)o.wis.size() - 1, 0);
                         cur_bin = (int)bin;
                     }
-                    bins[wi.bin_off + bin].y += 1;
+                    o.bins[bin].y += 1;
                     wi_pts = 0;
                     // tile of this bin must stay inside the grid
                     for (int k = 0; k < dw; ++k) {
                         const int lo = bc[k] * B - m + 1, hi = bc[k] * B + B + m - 1;
-                        if (lo < 0 || hi >= nos)
-                            return fail(ANOVA_ERR_INVALID_ARG, "bandwidth N too small for this window cut-off m");
+                        if (lo < 0 || hi >= nos) o.bad = true;
                     }
+                    if (o.bad) return;
                 }
-                wis.back().z = (int)segs.size();
+                o.wis.back().z = (int)o.segs.size();
                 prev = key;
             }
-            segs.back().z += 1;
+            o.segs.back().z += 1;
             wi_pts += 1;
         }
+        for (int k = 0; k < 3; ++k) { o.cmin[k] = cmin[k]; o.cmax[k] = cmax[k]; }
+    };
+    parallel_for_threads(P, 1, [&](int t, int nt) {
+        for (int w = t; w < P; w += nt) build_window(w);
+    });
+    for (int w = 0; w < P; ++w) {
+        WindowInfo &wi = p->win[w];
+        const WinTables &o = wt[w];
+        if (o.bad) return fail(ANOVA_ERR_INVALID_ARG, "bandwidth N too small for this window cut-off m");
+        const int dw = wi.dw;
+        const int s0 = (int)segs.size(), x0 = (int)wis.size();
+        wi.seg_begin = s0;
+        wi.wi_begin = x0;
+        wi.bin_off = (int)bins.size();
+        segs.insert(segs.end(), o.segs.begin(), o.segs.end());
+        for (int4 t : o.wis) wis.push_back(make_int4(t.x, t.y + s0, t.z + s0, t.w));
+        for (int2 b : o.bins) bins.push_back(b.y > 0 ? make_int2(b.x + x0, b.y) : b);
         wi.seg_end = (int)segs.size();
         wi.wi_end = (int)wis.size();
         for (int k = 0; k < dw; ++k) {
-            wi.box_lo[k] = cmin[k] - m + 1;
-            wi.box_hi[k] = cmax[k] + m + 1;
+            wi.box_lo[k] = o.cmin[k] - m + 1;
+            wi.box_hi[k] = o.cmax[k] + m + 1;
         }
         wi.grid_off = goff;
         int64_t gsz = 1;
@@ -612,6 +681,22 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
             }
         }
     }
+    // FFT tiles over whole grids, for products from grids summed over several plans' points
+    // (the sum is not confined to this plan's box)
+    std::vector<int4> ftiles_full;
+    for (Group &g : p->groups) {
+        for (int pass = 0; pass < g.dw; ++pass) {
+            for (int w = g.w_begin; w < g.w_end; ++w) {
+                WindowInfo &wi = p->win[w];
+                wi.full_begin[pass] = (int)ftiles_full.size();
+                const int phi = g.dw == 3 ? nos : 1, qhi = g.dw >= 2 ? nos : 1;
+                for (int pp = 0; pp < phi; ++pp)
+                    for (int q = 0; q < qhi; q += kConvLines)
+                        ftiles_full.push_back(make_int4(w, pp, q, pass | (std::min(kConvLines, qhi - q) << 8)));
+                wi.full_end[pass] = (int)ftiles_full.size();
+            }
+        }
+    }
     // bins holding several work items (their partial tiles are summed before the grid gather)
     std::vector<int4> mbins;
     for (int w = 0; w < P; ++w) {
@@ -637,17 +722,25 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         std::vector<int> hperm(total);
         ANOVA_CUDA_TRY(cudaMemcpyAsync(hperm.data(), p->perm, sizeof(int) * total, cudaMemcpyDeviceToHost, st));
         ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<char> seen(n);
-        for (int w = 0; w < P; ++w) {
-            std::fill(seen.begin(), seen.end(), 0);
-            for (long long q = (long long)w * n; q < (long long)(w + 1) * n; ++q) {
-                const int i = hperm[q];
-                if (i < 0 || i >= n || seen[i]) return fail(ANOVA_ERR_CUDA, "plan check: sort did not produce a permutation");
-                seen[i] = 1;
-                if (q > (long long)w * n && hkeys[q] < hkeys[q - 1])
-                    return fail(ANOVA_ERR_CUDA, "plan check: keys not sorted");
-                if ((int)(hkeys[q] >> KB) != w) return fail(ANOVA_ERR_CUDA, "plan check: window order");
+        // windows checked on host threads: 1 = not a permutation, 2 = not sorted, 3 = window order
+        std::vector<int> perr(P, 0);
+        parallel_for_threads(P, 1, [&](int t, int nt) {
+            std::vector<char> seen(n);
+            for (int w = t; w < P; w += nt) {
+                std::fill(seen.begin(), seen.end(), 0);
+                for (long long q = (long long)w * n; q < (long long)(w + 1) * n; ++q) {
+                    const int i = hperm[q];
+                    if (i < 0 || i >= n || seen[i]) { perr[w] = 1; break; }
+                    seen[i] = 1;
+                    if (q > (long long)w * n && hkeys[q] < hkeys[q - 1]) { perr[w] = 2; break; }
+                    if ((int)(hkeys[q] >> KB) != w) { perr[w] = 3; break; }
+                }
             }
+        });
+        for (int e : perr) {
+            if (e == 1) return fail(ANOVA_ERR_CUDA, "plan check: sort did not produce a permutation");
+            if (e == 2) return fail(ANOVA_ERR_CUDA, "plan check: keys not sorted");
+            if (e == 3) return fail(ANOVA_ERR_CUDA, "plan check: window order");
         }
         const int tw = B + 2 * m - 1;
         for (int w = 0; w < P; ++w) {
@@ -695,7 +788,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     return fail(ANOVA_ERR_CUDA, "plan check: grid box");
             (void)tw;
         }
-        for (const int4 &t : ftiles) {
+        for (const std::vector<int4> *tl : {&ftiles, &ftiles_full})
+        for (const int4 &t : *tl) {
             const int ax = t.w & 255, lines = t.w >> 8;
             if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || lines < 1 || lines > kConvLines ||
                 t.z + lines > nos || ax >= p->win[t.x].dw)
@@ -762,18 +856,16 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     if ((s = upload((void **)&p->bins, bins.data(), sizeof(int2) * bins.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->mbins, mbins.data(), sizeof(int4) * mbins.size())) != ANOVA_OK) return s;
     {
-        // cell index inside its bin for every sorted point (the low digits of the sort key)
-        std::vector<unsigned char> loc(total);
-        for (long long q = 0; q < total; ++q) {
-            const int w = (int)(hkeys[q] >> KB);
-            uint32_t bvol = 1;
-            for (int k = 0; k < p->win[w].dw; ++k) bvol *= (uint32_t)B;
-            loc[q] = (unsigned char)((hkeys[q] & kmask) % bvol);
-        }
-        if ((s = upload((void **)&p->cellloc, loc.data(), loc.size())) != ANOVA_OK) return s;
-        ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+        // cell index inside its bin for every sorted point (the low digits of the sort key), from
+        // the sorted keys still on the device
+        if ((s = upload((void **)&p->cellloc, nullptr, (size_t)total)) != ANOVA_OK) return s;
+        const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+        k_cellloc<<<nb, 256, 0, st>>>(kin, total, KB, B, (const int *)ddws.p, p->cellloc);
+        ANOVA_CUDA_TRY(cudaGetLastError());
     }
     if ((s = upload((void **)&p->ftiles, ftiles.data(), sizeof(int4) * ftiles.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->ftiles_full, ftiles_full.data(), sizeof(int4) * ftiles_full.size())) != ANOVA_OK)
+        return s;
     if ((s = upload((void **)&p->dwin, hdw.data(), sizeof(DevWindow) * P)) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->dev_status, nullptr, sizeof(int) * kStatusAlloc)) != ANOVA_OK) return s;
     ANOVA_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int) * kStatusAlloc, st));
