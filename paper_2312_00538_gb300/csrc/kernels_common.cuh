@@ -57,7 +57,6 @@ cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
 // passed by value so that they live in the kernel-parameter constant bank.
 struct WinParams {
     float c[16][kPolyDeg + 1];    // c[j][p]: psi(f + m - 1 - j) ~ sum_p c z^p, z = 2f - 1 (FP32)
-    float2 c2[8][kPolyDeg + 1];   // the same for j < 8, each coefficient duplicated (paired FMAs)
     double c64[8][kPolyDeg64 + 1];// the same for j < m in FP64 (degree 13, error ~1e-14)
     double beta;                  // Kaiser-Bessel shape pi (2 - 1/oversampling)
     double scale;                 // m / sinh(beta m): normalises psi(0) to 1
@@ -161,31 +160,6 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) { return __ffma
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f32x2 zero2() { return make_float2(0.0f, 0.0f); }
-// The weights of two coordinates at once (fx -> wx, fy -> wy) with paired FMAs: every lane of a
-// pair performs exactly the operations of Weights<float, M>::eval, so the values are identical,
-// in half the instructions. Coefficients come from wp.c2 (each coefficient duplicated into a pair).
-template <int M>
-__device__ __forceinline__ void weights_pair(float fx, float fy, const WinParams &wp, float *wx, float *wy) {
-    static_assert(kPolyDeg % 2 == 1, "even/odd split assumes an odd degree");
-    const f32x2 z = __ffma2_rn(make_float2(2.0f, 2.0f), make_float2(fx, fy), make_float2(-1.0f, -1.0f));
-    const f32x2 z2 = __fmul2_rn(z, z);
-    const f32x2 nz = make_float2(-z.x, -z.y);
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        f32x2 e = wp.c2[j][kPolyDeg - 1], o = wp.c2[j][kPolyDeg];
-#pragma unroll
-        for (int p = kPolyDeg - 3; p >= 0; p -= 2) {
-            e = __ffma2_rn(e, z2, wp.c2[j][p]);
-            o = __ffma2_rn(o, z2, wp.c2[j][p + 1]);
-        }
-        const f32x2 lo = __ffma2_rn(z, o, e), hi = __ffma2_rn(nz, o, e);
-        wx[j] = lo.x;
-        wy[j] = lo.y;
-        wx[2 * M - 1 - j] = hi.x;
-        wy[2 * M - 1 - j] = hi.y;
-    }
-}
-
 // two pairs from one 16-byte aligned shared-memory load
 __device__ __forceinline__ void lds_pairs(const float *p, f32x2 &a, f32x2 &b) {
     const float4 t = *reinterpret_cast<const float4 *>(p);

@@ -311,8 +311,6 @@ WinParams make_winparams(const anova_plan *p) {
     WinParams wp{};
     for (int j = 0; j < 2 * p->m && j < 16; ++j)
         for (int q = 0; q <= kPolyDeg; ++q) wp.c[j][q] = (float)p->poly[(size_t)j * (kPolyDeg + 1) + q];
-    for (int j = 0; j < 2 * p->m && j < 8; ++j)
-        for (int q = 0; q <= kPolyDeg; ++q) wp.c2[j][q] = make_float2(wp.c[j][q], wp.c[j][q]);
     for (int j = 0; j < p->m && j < 8; ++j)
         for (int q = 0; q <= kPolyDeg64; ++q) wp.c64[j][q] = p->poly64[(size_t)j * (kPolyDeg64 + 1) + q];
     wp.beta = kb_beta();

@@ -23,11 +23,8 @@
 #ifndef ANOVA_SPREAD_MINB
 #define ANOVA_SPREAD_MINB 3  // resident CTAs per SM the packed FP32 spread is compiled for
 #endif
-#ifndef ANOVA_WEIGHTS_PAIR
-#define ANOVA_WEIGHTS_PAIR 0  // x and y window weights with paired FMAs (same values)
-#endif
 #ifndef ANOVA_EPI_PAIR
-#define ANOVA_EPI_PAIR 0  // tensor-core interpolation: b-sums of the epilogue with paired FMAs
+#define ANOVA_EPI_PAIR 1  // tensor-core interpolation: b-sums of the epilogue with paired FMAs
 #endif
 #ifndef ANOVA_SPREAD_UNROLL
 #define ANOVA_SPREAD_UNROLL 8  // points per unrolled group of the packed FP32 spread's inner loop
@@ -414,12 +411,8 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
             // stage the current batch's weights (zeros for lanes past the batch)
             {
                 float wx[W2], wy[W2], wz[W2];
-#if ANOVA_WEIGHTS_PAIR
-                weights_pair<M>(fx, fy, a.wp, wx, wy);
-#else
                 Weights<float, M>::eval(fx, a.wp, wx);
                 Weights<float, M>::eval(fy, a.wp, wy);
-#endif
                 Weights<float, M>::eval(fz, a.wp, wz);
                 const float vl = lane < cnt ? vv : 0.0f;
 #pragma unroll
@@ -1136,12 +1129,8 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
         // on failures at the next barrier.
         auto finish = [&](int bf, const Chunk &ch, const Raw &rw) {
             float wx[W2], wy[W2];
-#if ANOVA_WEIGHTS_PAIR
-            weights_pair<M>(rw.f[0], rw.f[1], a.wp, wx, wy);
-#else
             Weights<float, M>::eval(rw.f[0], a.wp, wx);
             Weights<float, M>::eval(rw.f[1], a.wp, wy);
-#endif
             if (!tc::mbar_wait_bounded(&mbar[bf], (parity >> bf) & 1u, PARAM_WAIT ? a.wait_polls : C::kMaxPolls)) {
                 failed = true;
                 return;
