@@ -51,6 +51,13 @@ def parse():
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
     ap.add_argument("--rank", type=int, default=200, help="woodbury: preconditioner rank")
+    ap.add_argument("--err-tol", type=float, default=0.0,
+                    help="ipm_batch/serve5: pivoted-Cholesky tolerance (0: the workloads' stated rank 100; "
+                         "Table 1: 1e-5)")
+    ap.add_argument("--krylov-tol", type=float, default=1e-6,
+                    help="ipm_batch/serve5: relative residual of each Newton solve (workload 3's MINRES tol)")
+    ap.add_argument("--max-iter", type=int, default=150,
+                    help="ipm_batch/serve5: interior point iterations (C = 100 problems take 80-110)")
     ap.add_argument("--rates", default="1,2,5,10,20,50", help="serve5: arrival rates (requests/s)")
     ap.add_argument("--concurrency", type=int, default=8, help="ipm_batch: concurrent solves")
     ap.add_argument("--n-max", type=int, default=200_000, help="ipm_batch/serve: largest n")
@@ -509,7 +516,9 @@ def run_ipm_batch(args):
     probs = config4(count=args.count, n_hi=args.n_max)
     o = ab.svm_opts_default()
     o.rank = 100
-    o.max_iter = 100
+    o.max_iter = args.max_iter
+    o.err_tol = args.err_tol
+    o.krylov_tol = args.krylov_tol
     tol = 1e-6
     plist = [dict(X=p["X"], y=p["y"], C=p["C"], ell=p["sigma"], windows=p["windows"]) for p in probs]
     torch.cuda.synchronize()
@@ -535,7 +544,8 @@ def run_ipm_batch(args):
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": "%d SVM problems, n log-uniform [5e3, %d], d=9, C x sigma grid, rank 100, "
-                                   "gap 1e-6" % (args.count, args.n_max), "concurrency": args.concurrency},
+                                   "gap 1e-6" % (args.count, args.n_max), "concurrency": args.concurrency,
+                       "err_tol": args.err_tol, "krylov_tol": args.krylov_tol, "max_iter": args.max_iter},
             "plain": res["plain"], "batched": res["batched"], "results_identical": bool(same),
             "speedup": res["batched"]["solves_per_s"] / res["plain"]["solves_per_s"]}
     print(json.dumps(line), flush=True)
@@ -613,7 +623,9 @@ def run_serve5(args):
     from synth import config5
     o = ab.svm_opts_default()
     o.rank = 100
-    o.max_iter = 100
+    o.max_iter = args.max_iter
+    o.err_tol = args.err_tol
+    o.krylov_tol = args.krylov_tol
     tol = 1e-6
     rates = [float(x) for x in args.rates.split(",")]
     warm = config5(2, 1.0, seed=77, n_hi=20000)
@@ -662,7 +674,8 @@ def run_serve5(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "%d requests per rate, n log-uniform [1e4, %d], d in {6,9,12,15,18}, "
                                    "(C, sigma) grid, rank 100, gap 1e-6" % (args.count, args.n_max),
-                       "slots": args.concurrency, "budget_gib": args.budget_gib},
+                       "slots": args.concurrency, "budget_gib": args.budget_gib, "err_tol": args.err_tol,
+                       "krylov_tol": args.krylov_tol, "max_iter": args.max_iter},
             "per_rate": rows}
     print(json.dumps(line), flush=True)
     return 0
