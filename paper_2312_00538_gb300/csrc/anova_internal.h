@@ -31,6 +31,7 @@ constexpr int kConvLines = ANOVA_CONV_LINES;  // grid lines per CTA of an FFT pa
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
+constexpr int kTcChunkRows = 128;        // points per chunk of the tensor-core interpolation
 constexpr int kTcMinPointsPerItem = 512;  // mean points per work item for the tensor-core
                                           // interpolation (FP32, m = 4, 3-D windows)
 constexpr int kStatusAlloc = 128;      // ints of a plan's status/counter block (>= 1 + 3 x 32)
@@ -117,6 +118,10 @@ struct anova_plan {
     unsigned char *cellloc = nullptr;  // [P*n]: cell index inside its bin, (l0 B + l1) B + l2
     int4 *segs = nullptr;         // {cell packed, sorted start, count, window}
     int4 *wis = nullptr;          // {window, seg_begin, seg_end, tile origin packed}
+    int4 *chunks = nullptr;       // tensor-core interpolation chunks: up to kTcChunkRows
+                                  // consecutive points of one cell column of a work item,
+                                  // {sorted start, count, l0 | l1 << 8 (column in the bin), 0}
+    int *wi_chunk = nullptr;      // [nwi + 1]: work item x owns chunks [wi_chunk[x], wi_chunk[x + 1])
     int *wi_order = nullptr;      // per window: its work items by decreasing point count
     int *wi_gorder = nullptr;     // per dimension group: all its work items by decreasing point count
     int2 *bins = nullptr;         // per window per bin: {first work item, count}

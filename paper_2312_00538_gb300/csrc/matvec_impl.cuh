@@ -403,6 +403,8 @@ anova_status interp_stage(anova_plan *p, const Group &gr, int a0, int a1, int w0
         xa.wait_polls = p->wait_polls;
         xa.counters = counters;
         xa.order = order;
+        xa.chunks = p->chunks;
+        xa.wi_chunk = p->wi_chunk;
         cudaError_t e;
         // the tensor-core form pays a fixed cost per work item and per chunk of up to 128
         // points; it is used when work items are well filled (large n), else the SIMT form

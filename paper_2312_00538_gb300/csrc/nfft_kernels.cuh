@@ -793,6 +793,8 @@ struct InterpWiArgs {
                              // uses the full limit)
     const int *order;        // persistent kernels: work items of each window, largest first
     int *counters;           // persistent kernels: per-RHS work counters (zeroed before the launch)
+    const int4 *chunks;      // tensor-core path: chunks {sorted start, count, l0 | l1 << 8, 0}
+    const int *wi_chunk;     // tensor-core path: chunks of work item x: [wi_chunk[x], wi_chunk[x + 1])
 };
 
 template <int M, int B, int NWARP>
@@ -904,7 +906,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_interp3_x2(InterpWiArgs a) {
 // h_p[a, b] = sum_c z_p[c] g[l0 + a, l1 + b, l2_p + c], are one matrix product: the points' window
 // weights placed at their cell's offset l2_p in a row of 16 (the column's 11 grid values padded)
 // times the column's 64 x 16 block of the bin neighbourhood. A CTA of four warps takes up to 128
-// points of one column at a time (a chunk) and has the tensor cores form all their 64 inner sums
+// points of one column at a time (a chunk, cut once in the plan's chunk table) and has the tensor
+// cores form all their 64 inner sums
 // (tcgen05.mma kind::tf32, M = 128, N = 64, K = 2 x 8; both operands split into a tf32 high part
 // and an FP32 remainder so that hi*hi + hi*lo + lo*hi carries ~22 significant bits; FP32
 // accumulation in tensor memory). Each thread then reads its point's 64 sums from tensor memory
@@ -922,10 +925,11 @@ struct InterpTcCfg {
     static constexpr int NCOL = W2 * W2;             // rows (a, b) of the column block (MMA N)
     static constexpr int KC = 16;                    // column length TW padded to two K = 8 steps
     static constexpr uint32_t A_BYTES = ROWS * KC * 4, B_BYTES = NCOL * KC * 4;
-    // two buffers of {A hi, A lo} and of {B hi, B lo}, the neighbourhood, barriers, TMEM slot, work
-    static constexpr int SEG_CACHE = 128;            // segments of a work item kept in shared memory
-    static constexpr uint32_t A0 = 0, B0 = 4 * A_BYTES, TILE = B0 + 4 * B_BYTES, SEGS = TILE + TVP * 4,
-                              MBAR = SEGS + SEG_CACHE * 16, SLOT = MBAR + 16, WORK = SLOT + 4;
+    // two buffers of {A hi, A lo} and of {B hi, B lo}, the neighbourhood, the work item's chunks,
+    // barriers, TMEM slot, work
+    static constexpr int CHUNK_CACHE = 128;          // chunks of a work item kept in shared memory
+    static constexpr uint32_t A0 = 0, B0 = 4 * A_BYTES, TILE = B0 + 4 * B_BYTES, CHUNKS = TILE + TVP * 4,
+                              MBAR = CHUNKS + CHUNK_CACHE * 16, SLOT = MBAR + 16, WORK = SLOT + 4;
     static constexpr size_t smem = SLOT + 16;
     static constexpr uint32_t kMaxPolls = 1u << 22;
     static constexpr uint32_t TMEM_COLS = 2 * NCOL;  // two accumulators
@@ -950,12 +954,13 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     using C = InterpTcCfg<M, B>;
     constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS, KC = C::KC;
     static_assert(W2 == 8 && C::NCOL == 64 && B == 4, "layout written for m = 4, B = 4");
+    static_assert(ROWS == kTcChunkRows, "chunk table cut for this chunk size");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw + C::TILE);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + C::MBAR);
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem_raw + C::SLOT);
     int *work_s = reinterpret_cast<int *>(smem_raw + C::WORK);
-    int4 *segs_s = reinterpret_cast<int4 *>(smem_raw + C::SEGS);
+    int4 *chunks_s = reinterpret_cast<int4 *>(smem_raw + C::CHUNKS);
 
     const int r = blockIdx.y;
     const int t = threadIdx.x, warp = t >> 5;
@@ -1018,36 +1023,23 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                 tile[e] = grid[((long long)(o0 + x) * a.n_os + (o1 + y)) * a.n_os + (o2 + z)];
             }
         }
-        // the item's segments (the chunk walk reads them serially)
-        const bool seg_cached = wi.z - wi.y <= C::SEG_CACHE;
-        if (seg_cached)
-            for (int i = t; i < wi.z - wi.y; i += 128) segs_s[i] = a.segs[wi.y + i];
+        // the item's chunks (up to ROWS consecutive points of one column; the plan's chunk
+        // table) in shared memory
+        const int ch0 = a.wi_chunk[wi_idx], ch1 = a.wi_chunk[wi_idx + 1];
+        const bool ch_cached = ch1 - ch0 <= C::CHUNK_CACHE;
+        if (ch_cached)
+            for (int i = t; i < ch1 - ch0; i += 128) chunks_s[i] = a.chunks[ch0 + i];
         __syncthreads();
-        auto seg_at = [&](int i) -> int4 { return seg_cached ? segs_s[i - wi.y] : a.segs[i]; };
-
-        // chunk cursor over the item's segments: up to ROWS consecutive points of one column
-        int cs = wi.y, coff = 0;
+        int cc = ch0;
         auto form = [&](Chunk &ch) {
             ch.cnt = 0;
-            if (cs >= wi.z) return;
-            int4 sg = seg_at(cs);
-            const int cx = cell_coord(sg.x, 0), cy = cell_coord(sg.x, 1);
-            ch.q0 = sg.y + coff;
-            ch.l0 = cx - bin[0] * B;
-            ch.l1 = cy - bin[1] * B;
-            while (true) {
-                const int take = min(sg.z - coff, ROWS - ch.cnt);
-                ch.cnt += take;
-                coff += take;
-                if (coff == sg.z) {
-                    ++cs;
-                    coff = 0;
-                    if (cs >= wi.z) break;
-                    sg = seg_at(cs);
-                    if (cell_coord(sg.x, 0) != cx || cell_coord(sg.x, 1) != cy) break;
-                }
-                if (ch.cnt == ROWS) break;
-            }
+            if (cc >= ch1) return;
+            const int4 d = ch_cached ? chunks_s[cc - ch0] : a.chunks[cc];
+            ++cc;
+            ch.q0 = d.x;
+            ch.cnt = d.y;
+            ch.l0 = d.z & 255;
+            ch.l1 = d.z >> 8;
         };
         auto load_raw = [&](const Chunk &ch, Raw &rw) {
             if (t < ch.cnt) {

@@ -333,7 +333,7 @@ void destroy_plan(anova_plan *p) {
     }
     if (p->fork_evt) cudaEventDestroy(p->fork_evt);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->chunks, p->wi_chunk, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -711,6 +711,34 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         wi.mb_end = (int)mbins.size();
     }
     p->nmbins = (int)mbins.size();
+    // chunks of the tensor-core interpolation: a work item's points are sorted by cell, so the
+    // cells of one column (l0, l1) of its bin are consecutive; each column is cut into runs of
+    // at most kTcChunkRows points
+    std::vector<int4> chunks;
+    std::vector<int> wi_chunk(wis.size() + 1, 0);
+    for (size_t x = 0; x < wis.size(); ++x) {
+        const int4 t = wis[x];
+        wi_chunk[x] = (int)chunks.size();
+        int cur_col = -1;
+        for (int s2 = t.y; s2 < t.z; ++s2) {
+            const int4 sg = segs[s2];
+            const int l0 = ((sg.x >> 0) & 1023) - ((t.w >> 0) & 1023) * B;
+            const int l1 = ((sg.x >> 10) & 1023) - ((t.w >> 10) & 1023) * B;
+            const int col = l0 | (l1 << 8);
+            int q = sg.y, left = sg.z;
+            while (left > 0) {
+                if (col != cur_col || chunks.back().y == kTcChunkRows) {
+                    chunks.push_back(make_int4(q, 0, col, 0));
+                    cur_col = col;
+                }
+                const int take = std::min(left, kTcChunkRows - chunks.back().y);
+                chunks.back().y += take;
+                q += take;
+                left -= take;
+            }
+        }
+    }
+    wi_chunk[wis.size()] = (int)chunks.size();
     p->nseg = (int)segs.size();
     p->nwi = (int)wis.size();
     p->ntiles = (int)ftiles.size();
@@ -788,6 +816,20 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     return fail(ANOVA_ERR_CUDA, "plan check: grid box");
             (void)tw;
         }
+        for (size_t x = 0; x < wis.size(); ++x) {
+            // a work item's chunks cover its points in order, each inside one column of its bin
+            const int4 t = wis[x];
+            long long q = segs[t.y].y;
+            if (wi_chunk[x] > wi_chunk[x + 1]) return fail(ANOVA_ERR_CUDA, "plan check: chunk table");
+            for (int c = wi_chunk[x]; c < wi_chunk[x + 1]; ++c) {
+                const int4 ch = chunks[c];
+                const int l0 = ch.z & 255, l1 = ch.z >> 8;
+                if (ch.x != q || ch.y < 1 || ch.y > kTcChunkRows || l0 < 0 || l0 >= B || l1 < 0 || l1 >= B)
+                    return fail(ANOVA_ERR_CUDA, "plan check: chunk table");
+                q += ch.y;
+            }
+            if (q != (long long)segs[t.z - 1].y + segs[t.z - 1].z) return fail(ANOVA_ERR_CUDA, "plan check: chunk table");
+        }
         for (const std::vector<int4> *tl : {&ftiles, &ftiles_full})
         for (const int4 &t : *tl) {
             const int ax = t.w & 255, lines = t.w >> 8;
@@ -822,6 +864,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     anova_status s;
     if ((s = upload((void **)&p->segs, segs.data(), sizeof(int4) * segs.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->wis, wis.data(), sizeof(int4) * wis.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->chunks, chunks.data(), sizeof(int4) * chunks.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->wi_chunk, wi_chunk.data(), sizeof(int) * wi_chunk.size())) != ANOVA_OK) return s;
     {
         // each window's work items by decreasing point count (ties by index): persistent kernels
         // that take items in this order finish on the smallest ones
