@@ -233,7 +233,8 @@ void anova_model_destroy(anova_model_t model);
  * anova_nfft_plan_tuned -- anova_nfft_plan_ex (same arguments and errors) followed by a search
  * over launch settings that leave the arithmetic of each point-window product unchanged; the
  * fastest plan is returned. Settings: the points-per-work-item cap of the spread/interpolation
- * work items (1024, 2048, 4096; each needs its own plan tables); for FP32 plans with m = 4 and a
+ * work items (1024, 2048, 4096) and then, at the best cap, the grid lines per CTA of the FFT passes
+ * (8, 16, 32) (each needs its own plan tables); for FP32 plans with m = 4 and a
  * 3-D window, the tensor-core or the FP32-pipe interpolation (unless `flags` fixes one); right-hand
  * sides per pass (16, 8, 4, below nrhs); for FP64 plans with P >= 2, windows on concurrent streams
  * or not. Each setting is timed over `reps` matvecs with `nrhs` columns (after one warm-up call)
@@ -242,7 +243,7 @@ void anova_model_destroy(anova_model_t model);
  * nrhs in [1, 1024], reps in [1, 1000]; report (may be NULL) receives the choice:
  *   wi_max, interp (ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT, 0 if not searched), rhs_chunk,
  *   fork_windows (0/1, 0 if not searched), candidates (settings timed), ms (mean ms per matvec at
- *   the choice), ms_default (the same with anova_nfft_plan_ex's settings).
+ *   the choice), ms_default (the same with anova_nfft_plan_ex's settings), conv_lines.
  * Allocates n * nrhs elements twice for the timing inputs and frees them before returning.
  * Errors: those of anova_nfft_plan_ex; INVALID_ARG (nrhs, reps); TIMEOUT (a kernel wait ran out).
  */
@@ -254,6 +255,7 @@ typedef struct {
     int candidates;
     double ms;
     double ms_default;
+    int conv_lines;
 } anova_tune_report;
 
 anova_status anova_nfft_plan_tuned(const double *points, int64_t n, int d, const int32_t *windows,

@@ -224,7 +224,7 @@ def anova_nfft_plan_ex(points, windows, ell, eta=None, N=32, m=4, flags=ANOVA_FP
 class anova_tune_report(ctypes.Structure):
     _fields_ = [("wi_max", ctypes.c_int), ("interp", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
                 ("fork_windows", ctypes.c_int), ("candidates", ctypes.c_int), ("ms", ctypes.c_double),
-                ("ms_default", ctypes.c_double)]
+                ("ms_default", ctypes.c_double), ("conv_lines", ctypes.c_int)]
 
 
 def anova_nfft_plan_tuned(points, windows, ell, eta=None, N=32, m=4, flags=ANOVA_FP32, nrhs=1, reps=5,

@@ -23,11 +23,17 @@ constexpr int kWiMax = ANOVA_WI_MAX;  // points per spread work item (at most)
 #ifndef ANOVA_F64_B
 #define ANOVA_F64_B 4
 #endif
-constexpr int kBinF64 = ANOVA_F64_B;   // cells per bin edge of FP64 plans (FP32: 4)
+constexpr int kBinF64 = ANOVA_F64_B;   // cells per bin edge of FP64 plans
+#ifndef ANOVA_F32_B
+#define ANOVA_F32_B 4
+#endif
+constexpr int kBinF32 = ANOVA_F32_B;   // cells per bin edge of FP32 plans
+// a point's cell index inside its bin is stored in one byte
+static_assert(kBinF32 * kBinF32 * kBinF32 <= 256 && kBinF64 * kBinF64 * kBinF64 <= 256, "bin too large");
 #ifndef ANOVA_CONV_LINES
 #define ANOVA_CONV_LINES 16
 #endif
-constexpr int kConvLines = ANOVA_CONV_LINES;  // grid lines per CTA of an FFT pass (even, <= 32)
+constexpr int kConvLines = ANOVA_CONV_LINES;  // default grid lines per CTA of an FFT pass (8, 16 or 32)
 constexpr int kPolyDeg = 7;            // Horner degree of the FP32 window polynomials
 constexpr int kPolyDeg64 = 13;         // Horner degree of the FP64 window polynomials
 constexpr int kMaxWindows = 64;
@@ -143,6 +149,7 @@ struct anova_plan {
     cudaEvent_t fork_evt = nullptr, join_evt[3] = {nullptr, nullptr, nullptr};
     int interp_flags = 0;         // ANOVA_INTERP_TENSOR / ANOVA_INTERP_SIMT as created or tuned
     int wi_max = anova::kWiMax;   // points per work item (at most); set at plan creation
+    int conv_lines = anova::kConvLines;  // grid lines per CTA of an FFT pass (8, 16 or 32)
     int rhs_chunk = 16;           // right-hand sides per pass of the multi-RHS matvec (1..16)
     int fork_windows = 1;         // FP64: run windows of one dimension group on the aux streams
     unsigned wait_polls = 1u << 22;  // polls of a bounded tensor-core completion wait (about a
@@ -212,9 +219,15 @@ anova_status run_model_create_t(anova_plan *src, const void *w, anova_model *mod
 // Target half: interpolation at tgt's points from the model's grids, then the window sum.
 template <typename T>
 anova_status run_model_eval_t(const anova_model *model, anova_plan *tgt, void *f);
-// create_plan with an explicit work-item cap (kSegMax <= wi_max <= 1 << 16)
-anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_t *windows, int P,
-                            const double *ell, const double *eta, int N, int m, int flags, void *stream,
-                            int wi_max, anova_plan_t *out);
+// How a plan cuts its work (the arithmetic of a point-window product does not depend on it):
+// points per spread work item (kSegMax <= wi_max <= 1 << 16) and grid lines per CTA of an FFT
+// pass (8, 16 or 32).
+struct PlanShape {
+    int wi_max = kWiMax;
+    int conv_lines = kConvLines;
+};
+anova_status create_plan_shaped(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                                const double *ell, const double *eta, int N, int m, int flags, void *stream,
+                                const PlanShape &shape, anova_plan_t *out);
 void destroy_plan(anova_plan *p);
 }  // namespace anova

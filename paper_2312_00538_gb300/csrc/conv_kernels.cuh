@@ -139,19 +139,19 @@ __device__ __forceinline__ void conv_line(T (&re)[NOS / 32], T (&im)[NOS / 32], 
     }
 }
 
-template <typename T, int NOS>
+template <typename T, int NOS, int LINES>
 struct ConvCfg {
-    static constexpr int LT = kConvLines;  // grid lines per CTA (at most)
+    static constexpr int LT = LINES;       // grid lines per CTA (at most)
     static constexpr int LS = NOS + 1;     // padded line stride in shared memory
     static constexpr size_t smem = sizeof(T) * ((size_t)LT * LS + NOS + NOS);
 };
 
 // Strides of window grids: element (u_0, .., u_{d-1}) at sum_k u_k n_os^{d-1-k}.
-template <typename T, int NOS, int DW>
+template <typename T, int NOS, int DW, int LINES>
 __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     pdl_wait();
     pdl_trigger();
-    using C = ConvCfg<T, NOS>;
+    using C = ConvCfg<T, NOS, LINES>;
     constexpr int VPL = NOS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LT = C::LT;

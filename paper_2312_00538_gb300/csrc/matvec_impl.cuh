@@ -33,7 +33,7 @@ template <typename T>
 struct Prec;
 template <>
 struct Prec<float> {
-    static constexpr int B = 4;
+    static constexpr int B = kBinF32;
     static constexpr int SPREAD_WARPS = ANOVA_SPREAD_WARPS;
     static constexpr int INTERP_WARPS = 8;
 };
@@ -69,10 +69,10 @@ cudaError_t launch_interp_t(const InterpArgs &a, int nseg, int nrhs, cudaStream_
     return launch_k(kern, dim3((nseg + NW - 1) / NW, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
-template <typename T, int NOS, int DW>
+template <typename T, int NOS, int DW, int LINES>
 cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t st) {
-    using C = ConvCfg<T, NOS>;
-    auto kern = k_conv<T, NOS, DW>;
+    using C = ConvCfg<T, NOS, LINES>;
+    auto kern = k_conv<T, NOS, DW, LINES>;
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
@@ -285,23 +285,35 @@ cudaError_t dispatch_interp(int dw, int m, const InterpArgs &a, int nseg, int nr
     return cudaErrorInvalidValue;
 }
 
-template <typename T, int NOS>
+template <typename T, int NOS, int LINES>
 cudaError_t dispatch_conv_dw(int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
     switch (dw) {
-        case 1: return launch_conv_t<T, NOS, 1>(a, nt, nrhs, st);
-        case 2: return launch_conv_t<T, NOS, 2>(a, nt, nrhs, st);
-        case 3: return launch_conv_t<T, NOS, 3>(a, nt, nrhs, st);
+        case 1: return launch_conv_t<T, NOS, 1, LINES>(a, nt, nrhs, st);
+        case 2: return launch_conv_t<T, NOS, 2, LINES>(a, nt, nrhs, st);
+        case 3: return launch_conv_t<T, NOS, 3, LINES>(a, nt, nrhs, st);
     }
     return cudaErrorInvalidValue;
 }
 
+template <typename T, int NOS>
+cudaError_t dispatch_conv_lines(int lines, int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
+    switch (lines) {
+        case 8: return dispatch_conv_dw<T, NOS, 8>(dw, a, nt, nrhs, st);
+        case 16: return dispatch_conv_dw<T, NOS, 16>(dw, a, nt, nrhs, st);
+        case 32: return dispatch_conv_dw<T, NOS, 32>(dw, a, nt, nrhs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// one FFT pass over the tiles [a.tile_begin, a.tile_end) of a tile table cut at `lines` grid
+// lines per tile
 template <typename T>
-cudaError_t dispatch_conv(int n_os, int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
+cudaError_t dispatch_conv(int n_os, int lines, int dw, const ConvArgs &a, int nt, int nrhs, cudaStream_t st) {
     switch (n_os) {
-        case 32: return dispatch_conv_dw<T, 32>(dw, a, nt, nrhs, st);
-        case 64: return dispatch_conv_dw<T, 64>(dw, a, nt, nrhs, st);
-        case 128: return dispatch_conv_dw<T, 128>(dw, a, nt, nrhs, st);
-        case 256: return dispatch_conv_dw<T, 256>(dw, a, nt, nrhs, st);
+        case 32: return dispatch_conv_lines<T, 32>(lines, dw, a, nt, nrhs, st);
+        case 64: return dispatch_conv_lines<T, 64>(lines, dw, a, nt, nrhs, st);
+        case 128: return dispatch_conv_lines<T, 128>(lines, dw, a, nt, nrhs, st);
+        case 256: return dispatch_conv_lines<T, 256>(lines, dw, a, nt, nrhs, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -527,7 +539,7 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
             ca.zero_offset = 0;
             const int nt = ca.tile_end - ca.tile_begin;
             if (nt > 0) {
-                cudaError_t e = dispatch_conv<T>(p->n_os, gr.dw, ca, nt, nrhs, st);
+                cudaError_t e = dispatch_conv<T>(p->n_os, p->conv_lines, gr.dw, ca, nt, nrhs, st);
                 if (e != cudaSuccess) return cuda_fail(e, "conv launch");
                 p->launches += 1;
             }
@@ -682,7 +694,7 @@ anova_status from_grids_impl(anova_plan *p, const T *grids, T *Kv, int nrhs) {
                 ca.zero_offset = 0;
                 const int nt = ca.tile_end - ca.tile_begin;
                 if (nt > 0) {
-                    cudaError_t e = dispatch_conv<T>(p->n_os, gr.dw, ca, nt, nr, p->stream);
+                    cudaError_t e = dispatch_conv<T>(p->n_os, p->conv_lines, gr.dw, ca, nt, nr, p->stream);
                     if (e != cudaSuccess) return cuda_fail(e, "conv launch");
                     p->launches += 1;
                 }

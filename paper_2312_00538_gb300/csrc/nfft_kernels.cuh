@@ -953,7 +953,7 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
     pdl_trigger();
     using C = InterpTcCfg<M, B>;
     constexpr int W2 = C::W2, TW = C::TW, ROWS = C::ROWS, KC = C::KC;
-    static_assert(W2 == 8 && C::NCOL == 64 && B == 4, "layout written for m = 4, B = 4");
+    static_assert(W2 == 8 && C::NCOL == 64 && B <= 8, "layout written for m = 4, bins of at most 8 cells");
     static_assert(ROWS == kTcChunkRows, "chunk table cut for this chunk size");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw + C::TILE);
@@ -1080,9 +1080,13 @@ __global__ void __launch_bounds__(128, ANOVA_TC_INTERP_MINB) k_interp3_tc(Interp
                 };
                 switch (rw.l2) {
                     case 0: put(std::integral_constant<int, 0>()); break;
-                    case 1: put(std::integral_constant<int, 1>()); break;
-                    case 2: put(std::integral_constant<int, 2>()); break;
-                    default: put(std::integral_constant<int, 3>()); break;
+                    case 1: if constexpr (B > 1) put(std::integral_constant<int, 1>()); break;
+                    case 2: if constexpr (B > 2) put(std::integral_constant<int, 2>()); break;
+                    case 3: if constexpr (B > 3) put(std::integral_constant<int, 3>()); break;
+                    case 4: if constexpr (B > 4) put(std::integral_constant<int, 4>()); break;
+                    case 5: if constexpr (B > 5) put(std::integral_constant<int, 5>()); break;
+                    case 6: if constexpr (B > 6) put(std::integral_constant<int, 6>()); break;
+                    default: if constexpr (B > 7) put(std::integral_constant<int, 7>()); break;
                 }
             }
             const float *src = tile + ((ch.l0 + ba) * TW + (ch.l1 + bb)) * TW;

@@ -343,15 +343,18 @@ void destroy_plan(anova_plan *p) {
 anova_status create_plan(const double *points, int64_t n, int d, const int32_t *windows, int P,
                          const double *ell, const double *eta, int N, int m, int flags,
                          void *stream, anova_plan_t *out) {
-    return create_plan_wi(points, n, d, windows, P, ell, eta, N, m, flags, stream, kWiMax, out);
+    return create_plan_shaped(points, n, d, windows, P, ell, eta, N, m, flags, stream, PlanShape(), out);
 }
 
-anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_t *windows, int P,
-                            const double *ell, const double *eta, int N, int m, int flags, void *stream,
-                            int wi_max, anova_plan_t *out) {
+anova_status create_plan_shaped(const double *points, int64_t n, int d, const int32_t *windows, int P,
+                                const double *ell, const double *eta, int N, int m, int flags, void *stream,
+                                const PlanShape &shape, anova_plan_t *out) {
     // ------------------------------------------------------------------ validation
     if (!out) return fail(ANOVA_ERR_INVALID_ARG, "out is NULL");
+    const int wi_max = shape.wi_max;
     if (wi_max < kSegMax || wi_max > (1 << 16)) return fail(ANOVA_ERR_INVALID_ARG, "work-item cap out of range");
+    if (shape.conv_lines != 8 && shape.conv_lines != 16 && shape.conv_lines != 32)
+        return fail(ANOVA_ERR_INVALID_ARG, "FFT lines per CTA must be 8, 16 or 32");
     *out = nullptr;
     if (!points || !windows || !ell) return fail(ANOVA_ERR_INVALID_ARG, "NULL input pointer");
     if (n < 1 || n > (int64_t)1 << 30) return fail(ANOVA_ERR_INVALID_ARG, "n must be in [1, 2^30]");
@@ -420,7 +423,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
     p->prec = prec;
     p->interp_flags = flags & 6;
     p->wi_max = wi_max;
-    p->B = prec == ANOVA_FP64 ? kBinF64 : 4;
+    p->conv_lines = shape.conv_lines;
+    p->B = prec == ANOVA_FP64 ? kBinF64 : kBinF32;
     p->NB = p->n_os / p->B;
     p->tile_w = p->B + 2 * m - 1;
     p->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -675,8 +679,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                     if (pass == 1) { qlo = wi.box_lo[0]; qhi = wi.box_hi[0]; }
                 }
                 for (int pp = plo; pp < phi; ++pp)
-                    for (int q = qlo; q < qhi; q += kConvLines)
-                        ftiles.push_back(make_int4(w, pp, q, pass | (std::min(kConvLines, qhi - q) << 8)));
+                    for (int q = qlo; q < qhi; q += p->conv_lines)
+                        ftiles.push_back(make_int4(w, pp, q, pass | (std::min(p->conv_lines, qhi - q) << 8)));
                 wi.tile_end[pass] = (int)ftiles.size();
             }
         }
@@ -691,8 +695,8 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
                 wi.full_begin[pass] = (int)ftiles_full.size();
                 const int phi = g.dw == 3 ? nos : 1, qhi = g.dw >= 2 ? nos : 1;
                 for (int pp = 0; pp < phi; ++pp)
-                    for (int q = 0; q < qhi; q += kConvLines)
-                        ftiles_full.push_back(make_int4(w, pp, q, pass | (std::min(kConvLines, qhi - q) << 8)));
+                    for (int q = 0; q < qhi; q += p->conv_lines)
+                        ftiles_full.push_back(make_int4(w, pp, q, pass | (std::min(p->conv_lines, qhi - q) << 8)));
                 wi.full_end[pass] = (int)ftiles_full.size();
             }
         }
@@ -833,7 +837,7 @@ anova_status create_plan_wi(const double *points, int64_t n, int d, const int32_
         for (const std::vector<int4> *tl : {&ftiles, &ftiles_full})
         for (const int4 &t : *tl) {
             const int ax = t.w & 255, lines = t.w >> 8;
-            if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || lines < 1 || lines > kConvLines ||
+            if (t.x < 0 || t.x >= P || t.y < 0 || t.y >= nos || t.z < 0 || lines < 1 || lines > p->conv_lines ||
                 t.z + lines > nos || ax >= p->win[t.x].dw)
                 return fail(ANOVA_ERR_CUDA, "plan check: FFT tile");
         }

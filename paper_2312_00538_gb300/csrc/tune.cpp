@@ -15,6 +15,7 @@ anova_status create_plan(const double *points, int64_t n, int d, const int32_t *
                          const double *ell, const double *eta, int N, int m, int flags, void *stream,
                          anova_plan_t *out);
 
+
 namespace {
 
 struct Setting {
@@ -171,29 +172,44 @@ anova_status tune_plan(const double *points, int64_t n, int d, const int32_t *wi
         best_set = def;
         if (two_interp) best_set.interp = auto_interp(best);
     }
-    // other work-item caps need their own plan tables
-    for (int wi_max : {kWiMax / 2, kWiMax * 2}) {
+    // other plan shapes need their own plan tables: work-item caps first, then FFT lines per CTA
+    // at the best cap
+    PlanShape best_shape;
+    auto try_shape = [&](const PlanShape &sh) -> anova_status {
         anova_plan_t c = nullptr;
-        if ((s = create_plan_wi(points, n, d, windows, P, ell, eta, N, m, flags, stream, wi_max, &c)) != ANOVA_OK)
-            return s;
+        anova_status r = create_plan_shaped(points, n, d, windows, P, ell, eta, N, m, flags, stream, sh, &c);
+        if (r != ANOVA_OK) return r;
         cand_owner.p = c;
         Setting cs = def;
         double cms = 0.0;
-        if ((s = search(c, &cs, &cms)) != ANOVA_OK) return s;
+        if ((r = search(c, &cs, &cms)) != ANOVA_OK) return r;
         if (cms < best_ms) {
             destroy_plan(best);
             best = c;
             best_owner.p = c;
             best_set = cs;
             best_ms = cms;
+            best_shape = sh;
         } else {
             destroy_plan(c);
         }
         cand_owner.p = nullptr;
+        return ANOVA_OK;
+    };
+    for (int wi_max : {kWiMax / 2, kWiMax * 2}) {
+        PlanShape sh;
+        sh.wi_max = wi_max;
+        if ((s = try_shape(sh)) != ANOVA_OK) return s;
+    }
+    for (int lines : {8, 32}) {
+        PlanShape sh = best_shape;
+        sh.conv_lines = lines;
+        if ((s = try_shape(sh)) != ANOVA_OK) return s;
     }
     apply(best, best_set);
     if (report) {
         report->wi_max = best->wi_max;
+        report->conv_lines = best->conv_lines;
         report->interp = two_interp ? best_set.interp : 0;
         report->rhs_chunk = std::min(best_set.rhs_chunk, nrhs);
         report->fork_windows = fp64 && P >= 2 ? best_set.fork : 0;

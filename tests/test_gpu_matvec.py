@@ -315,8 +315,9 @@ def test_tensor_and_simt_interpolation_agree(env):
 
 
 def test_tuned_plan_matches_default_and_oracle(env):
-    """The autotuned plan (work-item cap, interpolation form, RHS per pass, FP64 window streams)
-    computes the default plan's K v up to the order of sums, and the direct sum within the bar."""
+    """The autotuned plan (work-item cap, FFT lines per CTA, interpolation form, RHS per pass,
+    FP64 window streams) computes the default plan's K v up to the order of sums, and the direct
+    sum within the bar."""
     torch, ab = env
     X = _clustered(60000, SEED_BASE + 60)
     X = np.column_stack([X, X[:, ::-1] * 0.9, np.roll(X, 1, axis=1)])
@@ -325,7 +326,10 @@ def test_tuned_plan_matches_default_and_oracle(env):
     plan, rep = ab.anova_nfft_plan_tuned(X, W, 1.0, N=32, m=4, flags=ab.ANOVA_FP32, nrhs=6, reps=2)
     assert rep["wi_max"] in (1024, 2048, 4096)
     assert rep["interp"] in (ab.ANOVA_INTERP_TENSOR, ab.ANOVA_INTERP_SIMT)
-    assert rep["rhs_chunk"] in (6, 4) and rep["candidates"] == 1 + 3 * 2 * 2
+    assert rep["conv_lines"] in (8, 16, 32)
+    # the default setting, then 4 settings on each of 5 plans (default shape, two work-item caps,
+    # two FFT line counts)
+    assert rep["rhs_chunk"] in (6, 4) and rep["candidates"] == 1 + 5 * 2 * 2
     assert 0 < rep["ms"] <= rep["ms_default"]
     got = _run(torch, ab, plan, V, torch.float32)
     ref_plan = ab.anova_nfft_plan(X, W, 1.0, N=32, m=4, flags=ab.ANOVA_FP32)
@@ -341,7 +345,8 @@ def test_tuned_plan_matches_default_and_oracle(env):
     V2 = matvec_vectors(2000, 2, SEED_BASE + 63)
     p64, rep64 = ab.anova_nfft_plan_tuned(cfg["X"], cfg["windows"], cfg["sigma"], N=64, m=6,
                                           flags=ab.ANOVA_FP64, nrhs=2, reps=2)
-    assert rep64["interp"] == 0 and rep64["fork_windows"] in (0, 1) and rep64["candidates"] == 1 + 3 * 2
+    assert rep64["interp"] == 0 and rep64["fork_windows"] in (0, 1) and rep64["candidates"] == 1 + 5 * 2
+    assert rep64["conv_lines"] in (8, 16, 32)
     got64 = _run(torch, ab, p64, V2, torch.float64)
     ref64 = ok.anova_matvec(cfg["X"], cfg["windows"], cfg["sigma"], V2)
     for r in range(2):
