@@ -60,6 +60,11 @@ def parse():
                     help="ipm_batch/serve5: interior point iterations (C = 100 problems take 80-110)")
     ap.add_argument("--rates", default="1,2,5,10,20,50", help="serve5: arrival rates (requests/s)")
     ap.add_argument("--concurrency", type=int, default=8, help="ipm_batch: concurrent solves")
+    ap.add_argument("--m-precise", type=int, default=0,
+                    help="ipm_batch/serve/serve5: window cut-off of the solver's FP64 plan (0: the library default)")
+    ap.add_argument("--m-refine", type=int, default=-1,
+                    help="ipm_batch/serve/serve5: window cut-off of the FP64 refinement plan (-1: the library "
+                         "default, 0: the FP64 plan serves both)")
     ap.add_argument("--n-max", type=int, default=200_000, help="ipm_batch/serve: largest n")
     ap.add_argument("--rate", type=float, default=1.0,
                     help="serve: mean arrival rate of requests (Poisson, requests/s)")
@@ -516,6 +521,10 @@ def run_ipm_batch(args):
     probs = config4(count=args.count, n_hi=args.n_max)
     o = ab.svm_opts_default()
     o.rank = 100
+    if args.m_precise:
+        o.m_precise = args.m_precise
+    if args.m_refine >= 0:
+        o.m_refine = args.m_refine
     o.max_iter = args.max_iter
     o.err_tol = args.err_tol
     o.krylov_tol = args.krylov_tol
@@ -545,7 +554,8 @@ def run_ipm_batch(args):
             "data": "synthetic",
             "config": {"workload": "%d SVM problems, n log-uniform [5e3, %d], d=9, C x sigma grid, rank 100, "
                                    "gap 1e-6" % (args.count, args.n_max), "concurrency": args.concurrency,
-                       "err_tol": args.err_tol, "krylov_tol": args.krylov_tol, "max_iter": args.max_iter},
+                       "err_tol": args.err_tol, "krylov_tol": args.krylov_tol, "max_iter": args.max_iter,
+                       "m_precise": o.m_precise, "m_refine": o.m_refine},
             "plain": res["plain"], "batched": res["batched"], "results_identical": bool(same),
             "speedup": res["batched"]["solves_per_s"] / res["plain"]["solves_per_s"]}
     print(json.dumps(line), flush=True)
@@ -565,6 +575,10 @@ def run_serve(args):
     probs = config4(count=args.count, n_hi=args.n_max)
     o = ab.svm_opts_default()
     o.rank = 100
+    if args.m_precise:
+        o.m_precise = args.m_precise
+    if args.m_refine >= 0:
+        o.m_refine = args.m_refine
     o.max_iter = 100
     tol = 1e-6
     torch.cuda.synchronize()
@@ -623,6 +637,10 @@ def run_serve5(args):
     from synth import config5
     o = ab.svm_opts_default()
     o.rank = 100
+    if args.m_precise:
+        o.m_precise = args.m_precise
+    if args.m_refine >= 0:
+        o.m_refine = args.m_refine
     o.max_iter = args.max_iter
     o.err_tol = args.err_tol
     o.krylov_tol = args.krylov_tol
@@ -675,7 +693,8 @@ def run_serve5(args):
             "config": {"workload": "%d requests per rate, n log-uniform [1e4, %d], d in {6,9,12,15,18}, "
                                    "(C, sigma) grid, rank 100, gap 1e-6" % (args.count, args.n_max),
                        "slots": args.concurrency, "budget_gib": args.budget_gib, "err_tol": args.err_tol,
-                       "krylov_tol": args.krylov_tol, "max_iter": args.max_iter},
+                       "krylov_tol": args.krylov_tol, "max_iter": args.max_iter, "m_precise": o.m_precise,
+                       "m_refine": o.m_refine},
             "per_rate": rows}
     print(json.dumps(line), flush=True)
     return 0

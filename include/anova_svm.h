@@ -143,11 +143,20 @@ typedef struct {
     const int32_t *windows;  /* P x 3 windows (-1 padded); NULL: consecutive 3-feature windows */
     int P;
     int N, m;                /* FP32 plan (default 32, 4) */
-    int N_precise, m_precise;/* FP64 plan for residuals and objectives (default 64, 6) */
+    int N_precise, m_precise;/* FP64 plan for the objectives, K (y .* alpha) and the
+                                preconditioner (default 64, 6) */
     int scale_features;      /* 1: min-max scale every feature into [-0.2, 0.2] first */
     void *cuda_stream;
     int krylov;              /* SVM_KRYLOV_MINRES (default) or SVM_KRYLOV_GMRES */
-    int autotune;            /* 1: both plans by anova_nfft_plan_tuned (nrhs 1, 3 reps); default 0 */
+    int autotune;            /* 1: every plan by anova_nfft_plan_tuned (nrhs 1, 3 reps); default 0 */
+    int m_refine;            /* window cut-off of a second FP64 plan (bandwidth N_precise) that
+                                gives the refinement residuals of the Newton solves and the
+                                FP64-operator MINRES (default 4; 0 or m_precise: the FP64 plan
+                                above serves both). Its error (~1e-8 relative at m = 4) is far below
+                                the Newton solves' residual tolerance; the objectives and the
+                                stopping test keep the FP64 plan above, and K (y .* alpha) is
+                                recomputed with it every 8 steps and before convergence is
+                                accepted */
 } svm_opts;
 
 typedef struct {

@@ -465,7 +465,8 @@ class svm_opts(ctypes.Structure):
                 ("windows", ctypes.POINTER(ctypes.c_int32)), ("P", ctypes.c_int),
                 ("N", ctypes.c_int), ("m", ctypes.c_int), ("N_precise", ctypes.c_int),
                 ("m_precise", ctypes.c_int), ("scale_features", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("krylov", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("krylov", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("m_refine", ctypes.c_int)]
 
 
 class svm_stats(ctypes.Structure):

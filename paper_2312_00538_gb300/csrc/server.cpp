@@ -76,6 +76,7 @@ int64_t svm_request_footprint(int64_t n, int P, const svm_opts *opts) {
     if (n < 1 || P < 1) return 0;
     const int64_t r = std::min<int64_t>(std::max(o.rank, 1), n);
     int64_t b = plan_bytes(n, P, o.N, o.m, 4, 4) + plan_bytes(n, P, o.N_precise, o.m_precise, 2, 8);
+    if (o.m_refine != 0 && o.m_refine != o.m_precise) b += plan_bytes(n, P, o.N_precise, o.m_refine, 2, 8);
     b += n * r * (8 + 4) + r * r * 8 * 2;  // low-rank factor (FP64 + FP32 panel) and Woodbury core
     if (o.precond == NYSTROM_RANDOM)
         b += n * r * 8 * 2 + ((r + 31) / 32) * ((r + 31) / 32) * 8192 * ((n + 2047) / 2048);  // K G, K Q, Q^T K Q

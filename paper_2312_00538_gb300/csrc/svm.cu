@@ -468,6 +468,7 @@ __global__ void k_gm_combine(const double *__restrict__ V, const double *__restr
 // ------------------------------------------------------------------ solver state
 struct Solver {
     anova_plan *p32 = nullptr, *p64 = nullptr;
+    anova_plan *p64r = nullptr;  // FP64 plan of the refinement residuals (may be p64)
     lowrank *lr = nullptr;
     cudaStream_t st = nullptr;
     long long n = 0;
@@ -509,13 +510,13 @@ struct Solver {
         return ANOVA_OK;
     }
 
-    // out = A x for the saddle matrix of eq. (Newton); precise selects the FP64 plan
+    // out = A x for the saddle matrix of eq. (Newton); precise selects the FP64 refinement plan
     anova_status apply(const double *x, double *out, bool precise) {
         const int nb = blocks_for(n);
         anova_status s;
         if (precise) {
             k_yx_f64<<<nb, 256, 0, st>>>(x, y, n, t64);
-            if ((s = run_matvec_t<double>(p64, t64, k64, 1, -1)) != ANOVA_OK) return s;
+            if ((s = run_matvec_t<double>(p64r, t64, k64, 1, -1)) != ANOVA_OK) return s;
             k_saddle_post<double><<<nb, 256, 0, st>>>(k64, x, y, theta, n, out);
         } else {
             k_yx_f32<<<nb, 256, 0, st>>>(x, y, n, t32);
@@ -846,6 +847,7 @@ void svm_opts_default(svm_opts *o) {
     o->m = 4;
     o->N_precise = 64;
     o->m_precise = 6;
+    o->m_refine = 4;
     o->scale_features = 0;
     o->cuda_stream = nullptr;
 }
@@ -864,7 +866,8 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         if (o.max_iter < 1 || o.krylov_max < 1 || o.refine_max < 1 || !(o.sigma_barrier > 0 && o.sigma_barrier < 1) ||
             (o.krylov != SVM_KRYLOV_MINRES && o.krylov != SVM_KRYLOV_GMRES) ||
             (o.krylov == SVM_KRYLOV_GMRES && o.krylov_max > 1000) || (o.autotune != 0 && o.autotune != 1) ||
-            !(o.gamma > 0 && o.gamma < 1) || !(o.krylov_tol > 0) || !(o.ell > 0))
+            !(o.gamma > 0 && o.gamma < 1) || !(o.krylov_tol > 0) || !(o.ell > 0) ||
+            (o.m_refine != 0 && (o.m_refine < 3 || o.m_refine > 6)))
             return fail(ANOVA_ERR_INVALID_ARG, "invalid svm_opts");
         bool has_pos = false, has_neg = false;
         for (int64_t i = 0; i < n; ++i) {
@@ -916,6 +919,15 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                                           ANOVA_FP64, o.cuda_stream, &p64)) != ANOVA_OK)
             return s;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64(p64, destroy_plan);
+        // the refinement residuals' FP64 plan: same points and bandwidth, a shorter window
+        anova_plan *p64r = p64;
+        if (o.m_refine != 0 && o.m_refine != o.m_precise &&
+            (s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_refine,
+                                        ANOVA_FP64, o.cuda_stream, 1, 3, nullptr, &p64r)
+                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_refine,
+                                          ANOVA_FP64, o.cuda_stream, &p64r)) != ANOVA_OK)
+            return s;
+        std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64r(p64r != p64 ? p64r : nullptr, destroy_plan);
         lowrank *lr = nullptr;
         if ((s = lowrank_build_impl(p64, o.precond, (int)std::min<int64_t>(o.rank, n), o.err_tol, o.seed, &lr)) != ANOVA_OK)
             return s;
@@ -924,6 +936,7 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
         Solver S;
         S.p32 = p32;
         S.p64 = p64;
+        S.p64r = p64r;
         S.lr = lr;
         S.st = p64->stream;
         S.n = n;

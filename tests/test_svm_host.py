@@ -26,11 +26,12 @@ def test_defaults_follow_table1(ab):
     assert o.err_tol == t["cholesky_err_tol"]
     assert o.stop == ab.SVM_STOP_GAP
     assert (o.N, o.m, o.N_precise, o.m_precise) == (32, 4, 64, 6)
+    assert o.m_refine == 4
     assert o.krylov == ab.SVM_KRYLOV_MINRES
     assert o.autotune == 0
 
 
-@pytest.mark.parametrize("case", ["labels", "one_class", "C", "tol", "opts", "krylov", "autotune"])
+@pytest.mark.parametrize("case", ["labels", "one_class", "C", "tol", "opts", "krylov", "autotune", "m_refine"])
 def test_invalid_solver_arguments(ab, case):
     X = np.zeros((6, 3))
     y = np.array([1.0, -1.0, 1.0, -1.0, 1.0, -1.0])
@@ -51,6 +52,8 @@ def test_invalid_solver_arguments(ab, case):
         o.krylov = 7
     if case == "autotune":
         o.autotune = 2
+    if case == "m_refine":
+        o.m_refine = 7
     with pytest.raises(ab.AnovaError) as ei:
         ab.svm_ipm_solve(X, y, C, tol, opts=o)
     assert ei.value.status == ab.ANOVA_ERR_INVALID_ARG
@@ -84,6 +87,10 @@ def test_request_footprint(ab):
     assert f(20_000, 3, o) < f(20_000, 3, hi)
     n, P, r = 50_000, 3, o.rank
     assert f(n, P, o) >= n * r * 12 + 8 * 4 * P * (2 * o.N_precise) ** 3
+    # the refinement's own FP64 plan is counted when it differs from the precise plan
+    one = ab.svm_opts_default()
+    one.m_refine = 0
+    assert f(n, P, one) < f(n, P, o)
 
 
 def test_request_footprint_counts_transient_work(ab):
