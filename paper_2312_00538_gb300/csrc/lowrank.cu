@@ -10,7 +10,7 @@
 //  * Woodbury (Sec. 5): A^ = Theta + Y L L^T Y, A^{-1} = Theta^{-1} - Theta^{-1} Y L M^{-1} L^T Y
 //    Theta^{-1}, M = I + L^T Theta^{-1} L (Y Theta^{-1} Y = Theta^{-1} since y_i^2 = 1). M is
 //    accumulated in FP64 from an FP32 copy of the n x r panel and factored by Cholesky on the
-//    device; the apply reads the FP32 panel twice.
+//    device; the apply reads the FP32 panel twice, its products accumulated in FP32 pairs.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,6 +21,7 @@
 #include "anova_internal.h"
 #include "../../include/anova_svm.h"
 #include "lowrank_internal.h"
+
 
 namespace anova {
 namespace {
@@ -369,62 +370,107 @@ __global__ void k_recip(const double *__restrict__ a, long long n, double *__res
         out[i] = 1.0 / a[i];
 }
 
-// h = y .* g ./ theta (with the stored reciprocals)
-__global__ void k_scaled_rhs(const double *__restrict__ y, const double *__restrict__ g,
-                             const double *__restrict__ itheta, long long n, double *__restrict__ h) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        h[i] = y[i] * g[i] * itheta[i];
-}
-
-// u_part[c](q) = sum_{i in chunk c} L(i, q) h_i. Grid: (row chunks, groups of 8 columns); one
-// warp per column, lanes over the chunk's rows.
+// rows per chunk of the apply's first panel product
 constexpr int kApplyRows = 1024;
 
-__global__ void __launch_bounds__(256) k_panel_t(const float *__restrict__ L, const double *__restrict__ h,
-                                                 long long n, int r, double *__restrict__ upart) {
+// The two n x r panel products of the apply in FP32 pairs instead of FP64 (GB300's FP64 pipe runs
+// at 1/64 of FP32): a product l * a with an FP32 factor a is split exactly into p + e
+// (e = fma(l, a, -p)), sums are carried as S + C with the rounding error of every addition to S
+// recovered exactly (two-sum) into C, and the FP64 operand is split into two FP32 parts
+// (a = fl32(h), b = fl32(h - a)). The result matches FP64 accumulation to ~2^-44 of the sum of
+// the terms' magnitudes.
+// (explicitly rounded operations: no contraction into fused multiply-adds may change them)
+__device__ __forceinline__ void two_sum_acc(float &S, float &C, float p) {
+    const float t = __fadd_rn(S, p);
+    const float bp = __fsub_rn(t, S);
+    C = __fadd_rn(C, __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    S = t;
+}
+__device__ __forceinline__ void pair_fma_acc(float &S, float &C, float l, float a, float b) {
+    const float p = __fmul_rn(l, a);
+    const float e = __fmaf_rn(l, a, -p);
+    two_sum_acc(S, C, p);
+    C = __fadd_rn(C, __fmaf_rn(l, b, e));
+}
+
+// h = y .* g ./ theta split into FP32 parts: ha = fl32(h), hb = fl32(h - ha)
+__global__ void k_scaled_rhs_split(const double *__restrict__ y, const double *__restrict__ g,
+                                   const double *__restrict__ itheta, long long n, float *__restrict__ ha,
+                                   float *__restrict__ hb) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double h = y[i] * g[i] * itheta[i];
+        const float a = __double2float_rn(h);
+        ha[i] = a;
+        hb[i] = __double2float_rn(h - (double)a);
+    }
+}
+
+// u_part[c](q) = sum_{i in chunk c} L(i, q) h_i in FP32 pairs. Grid: (row chunks, groups of 8
+// columns); one warp per column, lanes over the chunk's rows.
+__global__ void __launch_bounds__(256) k_panel_t_pair(const float *__restrict__ L, const float *__restrict__ ha,
+                                                      const float *__restrict__ hb, long long n, int r,
+                                                      double *__restrict__ upart) {
     const long long i0 = (long long)blockIdx.x * kApplyRows;
     const long long i1 = min(n, i0 + kApplyRows);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.y * 8 + warp;
     if (q >= r) return;
     const float *col = L + (long long)q * n;
-    double s = 0.0;
-    for (long long i = i0 + lane; i < i1; i += 32) s = fma((double)col[i], h[i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) upart[(long long)blockIdx.x * r + q] = s;
-}
-
-__global__ void k_panel_t_sum(const double *__restrict__ upart, int nchunks, int r, double *__restrict__ u) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r; q += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += upart[(long long)c * r + q];
-        u[q] = s;
+    float S = 0.0f, C = 0.0f;
+    for (long long i = i0 + lane; i < i1; i += 32) pair_fma_acc(S, C, col[i], ha[i], hb[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float So = __shfl_down_sync(0xffffffffu, S, o), Co = __shfl_down_sync(0xffffffffu, C, o);
+        two_sum_acc(S, C, So);
+        C = __fadd_rn(C, Co);
     }
+    if (lane == 0) upart[(long long)blockIdx.x * r + q] = (double)S + (double)C;
 }
 
-// x_i = g_i / theta_i - (y_i / theta_i) sum_q L(i, q) z_q for i < n; x_n = g_n / s_schur.
-// 32 rows per CTA (one per lane); the 8 warps split the columns q and their partial sums are
-// added in a fixed order.
-__global__ void __launch_bounds__(256) k_panel_n(const float *__restrict__ L, const double *__restrict__ itheta,
-                                                 const double *__restrict__ y, const double *__restrict__ g,
-                                                 const double *__restrict__ z, long long n, int r,
-                                                 double *__restrict__ x, const double *__restrict__ schur) {
-    extern __shared__ double sm[];
-    double *zs = sm;
-    double *ps = sm + r;
-    for (int q = threadIdx.x; q < r; q += blockDim.x) zs[q] = z[q];
+// u = sum of the chunks' partials: one warp per column, lanes over chunks, a fixed order
+__global__ void __launch_bounds__(256) k_panel_t_sum_warp(const double *__restrict__ upart, int nchunks, int r,
+                                                          double *__restrict__ u) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 8 + warp;
+    if (q >= r) return;
+    double s = 0.0;
+    for (int c = lane; c < nchunks; c += 32) s += upart[(long long)c * r + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) u[q] = s;
+}
+
+// x_i = g_i / theta_i - (y_i / theta_i) sum_q L(i, q) z_q for i < n; x_n = g_n / s_schur, the sum
+// over q in FP32 pairs (z split into FP32 parts in shared memory). 32 rows per CTA (one per lane);
+// the 8 warps split the columns q and their partial sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_panel_n_pair(const float *__restrict__ L, const double *__restrict__ itheta,
+                                                      const double *__restrict__ y, const double *__restrict__ g,
+                                                      const double *__restrict__ z, long long n, int r,
+                                                      double *__restrict__ x, const double *__restrict__ schur) {
+    extern __shared__ float smf[];
+    float *za = smf, *zb = smf + r;
+    float *ps = smf + 2 * r;  // [8][32] pairs
+    for (int q = threadIdx.x; q < r; q += blockDim.x) {
+        const double zq = z[q];
+        const float a = __double2float_rn(zq);
+        za[q] = a;
+        zb[q] = __double2float_rn(zq - (double)a);
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * 32 + lane;
-    double s = 0.0;
+    float S = 0.0f, C = 0.0f;
     if (i < n)
-        for (int q = warp; q < r; q += 8) s = fma((double)L[(long long)q * n + i], zs[q], s);
-    ps[warp * 32 + lane] = s;
+        for (int q = warp; q < r; q += 8) pair_fma_acc(S, C, L[(long long)q * n + i], za[q], zb[q]);
+    ps[2 * (warp * 32 + lane)] = S;
+    ps[2 * (warp * 32 + lane) + 1] = C;
     __syncthreads();
     if (warp == 0 && i < n) {
-        double t = 0.0;
+        float S0 = ps[2 * lane], C0 = ps[2 * lane + 1];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) t += ps[w * 32 + lane];
+        for (int w = 1; w < 8; ++w) {
+            two_sum_acc(S0, C0, ps[2 * (w * 32 + lane)]);
+            C0 = __fadd_rn(C0, ps[2 * (w * 32 + lane) + 1]);
+        }
+        const double t = (double)S0 + (double)C0;
         const double it = itheta[i];
         x[i] = g[i] * it - y[i] * it * t;
     }
@@ -952,13 +998,15 @@ anova_status woodbury_apply(lowrank *lr, const double *theta, const double *y, c
     cudaStream_t st = p->stream;
     const long long n = lr->n;
     const int r = lr->rank;
-    k_scaled_rhs<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(y, g, lr->itheta, n, lr->hbuf);
-    k_panel_t<<<dim3(lr->napply, (r + 7) / 8), 256, 0, st>>>(lr->L32, lr->hbuf, n, r, lr->upart);
-    k_panel_t_sum<<<grid_for(r, 128), 128, 0, st>>>(lr->upart, lr->napply, r, lr->u);
+    // hbuf (n doubles) holds the two FP32 parts of y .* g ./ theta
+    float *ha = reinterpret_cast<float *>(lr->hbuf), *hb = ha + n;
+    k_scaled_rhs_split<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(y, g, lr->itheta, n, ha, hb);
+    k_panel_t_pair<<<dim3(lr->napply, (r + 7) / 8), 256, 0, st>>>(lr->L32, ha, hb, n, r, lr->upart);
+    k_panel_t_sum_warp<<<(r + 7) / 8, 256, 0, st>>>(lr->upart, lr->napply, r, lr->u);
     // z = M^{-1} u = W^T (W u)
     k_trmv<<<(r + 7) / 8, 256, 0, st>>>(lr->Wl, r, 1, lr->u, lr->tmp2);
     k_trmv<<<(r + 7) / 8, 256, 0, st>>>(lr->Wc, r, 0, lr->tmp2, lr->z);
-    k_panel_n<<<(unsigned)((n + 31) / 32), 256, sizeof(double) * (r + 256), st>>>(
+    k_panel_n_pair<<<(unsigned)((n + 31) / 32), 256, sizeof(float) * (2 * r + 512), st>>>(
         lr->L32, lr->itheta, y, g, lr->z, n, r, x, with_schur ? lr->schur : nullptr);
     ANOVA_CUDA_TRY(cudaGetLastError());
     return ANOVA_OK;
