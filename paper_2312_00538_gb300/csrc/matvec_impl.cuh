@@ -47,10 +47,21 @@ struct Prec<double> {
     static constexpr int INTERP_WARPS = 4;
 };
 
+#ifndef ANOVA_F64_PAIR
+#define ANOVA_F64_PAIR 1  // FP64 3-D spread: footprint sums in FP32 pairs
+#endif
+
 template <typename T, int DW, int M>
 cudaError_t launch_spread_t(const SpreadArgs &a, int nblocks, int nrhs, cudaStream_t st) {
     constexpr int B = Prec<T>::B, NW = Prec<T>::SPREAD_WARPS;
     using C = SpreadCfg<T, DW, M, B, NW>;
+    if constexpr (sizeof(T) == 8 && DW == 3 && ANOVA_F64_PAIR) {
+        auto kp = k_spread3_pair<M, B, NW>;
+        static const cudaError_t configured_p =
+            cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+        if (configured_p != cudaSuccess) return configured_p;
+        return launch_k(kp, dim3(nblocks, nrhs), dim3(NW * 32), C::smem, st, a);
+    }
     auto kern = k_spread<T, DW, M, B, NW>;
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
