@@ -397,7 +397,7 @@ anova_status launch_reduce(anova_plan *p, int dw, int a0, int a1, void *grid0, l
 template <typename T>
 anova_status interp_stage(anova_plan *p, const Group &gr, int a0, int a1, int w0, const T *grid,
                           long long grid_stride, int nrhs, T *part, const WinParams &wp, cudaStream_t st,
-                          int *counters) {
+                          int *counters, T *pair_scratch = nullptr) {
     const int wi0 = p->win[a0].wi_begin, wi1 = p->win[a1 - 1].wi_end;
     const int s0 = p->win[a0].seg_begin, s1 = p->win[a1 - 1].seg_end;
     const bool packed = packed_path((int)sizeof(T), gr.dw, p->m);
@@ -460,7 +460,38 @@ anova_status interp_stage(anova_plan *p, const Group &gr, int a0, int a1, int w0
         da.q_begin = (long long)a0 * p->n;
         da.q_end = (long long)a1 * p->n;
         da.wp = wp;
-        cudaError_t e = dispatch_interp_direct<T>(gr.dw, p->m, da, nrhs, st);
+        cudaError_t e = cudaSuccess;
+        bool pair_done = false;
+        if constexpr (sizeof(T) == 8) {
+          if (ANOVA_F64_PAIR && gr.dw == 3 && pair_scratch && p->m >= 3 && p->m <= 6) {
+            pair_done = true;
+            // FP32-pair form: the windows' boxes as pairs in the scratch buffer, then the sums
+            GridPairArgs ga;
+            ga.grid = reinterpret_cast<const double *>(grid);
+            ga.pairs = reinterpret_cast<fpair *>(pair_scratch);
+            ga.dwin = p->dwin;
+            ga.grid_stride = grid_stride;
+            ga.w_begin = a0;
+            ga.w_end = a1;
+            ga.n_os = p->n_os;
+            ga.box_cum[0] = 0;
+            for (int w = a0; w < a1; ++w) ga.box_cum[w - a0 + 1] = ga.box_cum[w - a0] + p->win[w].box_volume();
+            const long long vol = ga.box_cum[a1 - a0];
+            e = launch_k(k_grid_pairs<3>, dim3((unsigned)((vol + 255) / 256), nrhs), dim3(256), 0, st, ga);
+            if (e == cudaSuccess) {
+                p->launches += 1;
+                const fpair *pg = reinterpret_cast<const fpair *>(pair_scratch);
+                const dim3 grd((unsigned)((da.q_end - da.q_begin + 127) / 128), nrhs);
+                switch (p->m) {
+                    case 3: e = launch_k(k_interp_pair<3>, grd, dim3(128), 0, st, da, pg); break;
+                    case 4: e = launch_k(k_interp_pair<4>, grd, dim3(128), 0, st, da, pg); break;
+                    case 5: e = launch_k(k_interp_pair<5>, grd, dim3(128), 0, st, da, pg); break;
+                    default: e = launch_k(k_interp_pair<6>, grd, dim3(128), 0, st, da, pg); break;
+                }
+            }
+          }
+        }
+        if (!pair_done) e = dispatch_interp_direct<T>(gr.dw, p->m, da, nrhs, st);
         if (e != cudaSuccess) return cuda_fail(e, "interp launch");
         p->launches += 1;
     } else if (wi1 > wi0) {
@@ -559,7 +590,9 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         stage_record(p, STAGE_FFT, e2, e3);
         // 4. interpolation
         {
-            anova_status is = interp_stage<T>(p, gr, a0, a1, w0, g[3], grid_stride, nrhs, part, wp, st, counters);
+            // g[0] is free once the first pass has read it (3-D windows: g0 -> g1 -> g2 -> g3)
+            anova_status is = interp_stage<T>(p, gr, a0, a1, w0, g[3], grid_stride, nrhs, part, wp, st, counters,
+                                              gr.dw == 3 ? g[0] : nullptr);
             if (is != ANOVA_OK) return is;
         }
         cudaEvent_t e4 = stage_event(p);
@@ -711,7 +744,7 @@ anova_status from_grids_impl(anova_plan *p, const T *grids, T *Kv, int nrhs) {
                 }
             }
             st = interp_stage<T>(p, gr, gr.w_begin, gr.w_end, 0, g[3], gs, nr, part, wp, p->stream,
-                                 p->dev_status + 1);
+                                 p->dev_status + 1, g[0]);
             if (st != ANOVA_OK) return st;
         }
         ANOVA_CUDA_TRY(launch_window_sum<T>(part, Kv + (size_t)r0 * p->n, p->n, nr, p->P, p->stream));

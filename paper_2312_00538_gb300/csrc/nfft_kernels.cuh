@@ -1584,6 +1584,100 @@ __global__ void __launch_bounds__(128) k_interp_direct(InterpDirectArgs<T> a) {
     a.part[((size_t)(w - a.part_w0) * a.nrhs + r) * a.n + a.perm[q]] = f;
 }
 
+// ------------------------------------------------------------------ FP64 3-D interpolation in FP32 pairs
+// k_interp_direct for the FP64 plans' 3-D windows with the multiply-adds on the FP32 pipe: the
+// convolved grid's box is first converted to pairs (hi = fl32(g), lo = fl32(g - hi)) in a free
+// workspace buffer, then every point's (2M)^3 block is summed as in k_interp_direct, the weights
+// evaluated in FP64 and split into pairs. Same pair arithmetic as k_spread3_pair.
+struct GridPairArgs {
+    const double *grid;
+    fpair *pairs;                 // same layout as grid
+    const DevWindow *dwin;
+    long long grid_stride;
+    long long box_cum[kMaxWindows + 1];  // cumulative box volumes of windows w_begin..
+    int w_begin, w_end, n_os;
+};
+
+template <int DW>
+__global__ void __launch_bounds__(256) k_grid_pairs(GridPairArgs a) {
+    static_assert(DW == 3, "3-D windows");
+    pdl_wait();
+    pdl_trigger();
+    const int r = blockIdx.y;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = a.w_end - a.w_begin;
+    if (idx >= a.box_cum[nw]) return;
+    int wl = 0;
+    while (idx >= a.box_cum[wl + 1]) ++wl;
+    const DevWindow dw = a.dwin[a.w_begin + wl];
+    long long loc = idx - a.box_cum[wl];
+    int u[3];
+    for (int k = 2; k >= 0; --k) {
+        const int ext = dw.box_hi[k] - dw.box_lo[k];
+        u[k] = dw.box_lo[k] + (int)(loc % ext);
+        loc /= ext;
+    }
+    const size_t g = (size_t)r * a.grid_stride + dw.grid_off + ((size_t)u[0] * a.n_os + u[1]) * a.n_os + u[2];
+    a.pairs[g] = fpair_of(a.grid[g]);
+}
+
+template <int M>
+__global__ void __launch_bounds__(128) k_interp_pair(InterpDirectArgs<double> a, const fpair *__restrict__ pairs) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int W2 = 2 * M;
+    const int r = blockIdx.y;
+    const long long q = a.q_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.q_end) return;
+    int lo = a.seg_begin, hi = a.seg_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].y <= q) lo = mid; else hi = mid - 1;
+    }
+    const int4 sg = a.segs[lo];
+    const int w = sg.w;
+    const DevWindow dw = a.dwin[w];
+    const fpair *grid = pairs + (size_t)r * a.grid_stride_rhs + dw.grid_off;
+    int c0[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c0[k] = cell_coord(sg.x, k) - M + 1;
+    fpair wt[3][W2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double wd[W2];
+        Weights<double, M>::eval(a.frac[(size_t)k * a.total + q], a.wp, wd);
+#pragma unroll
+        for (int c = 0; c < W2; ++c) wt[k][c] = fpair_of(wd[c]);
+    }
+    fpair f = {0.0f, 0.0f};
+    const long long n2 = (long long)a.n_os * a.n_os;
+#pragma unroll 1
+    for (int aa = 0; aa < W2; ++aa) {
+        fpair sa = {0.0f, 0.0f};
+        for (int bb = 0; bb < W2; ++bb) {
+            const float2 *row = reinterpret_cast<const float2 *>(grid + (long long)(c0[0] + aa) * n2 +
+                                                                 (long long)(c0[1] + bb) * a.n_os + c0[2]);
+            fpair sb = {0.0f, 0.0f};
+#pragma unroll
+            for (int cc = 0; cc < W2; ++cc) {
+                const float2 gv = __ldg(row + cc);
+                fpair_acc(sb, fpair_mul({gv.x, gv.y}, wt[2][cc]));
+            }
+            fpair wyb = wt[1][0];
+#pragma unroll
+            for (int k = 1; k < W2; ++k)
+                if (k == bb) wyb = wt[1][k];
+            fpair_acc(sa, fpair_mul(wyb, sb));
+        }
+        fpair wxa = wt[0][0];
+#pragma unroll
+        for (int k = 1; k < W2; ++k)
+            if (k == aa) wxa = wt[0][k];
+        fpair_acc(f, fpair_mul(wxa, sa));
+    }
+    a.part[((size_t)(w - a.part_w0) * a.nrhs + r) * a.n + a.perm[q]] = (double)f.hi + (double)f.lo;
+}
+
 // ------------------------------------------------------------------ sum over windows
 // Kv[r][j] = sum over windows w (in order) of part[w][r][j]; blockIdx.y = r. VEC = 4: four
 // consecutive j per thread with 16-byte loads (n a multiple of 4 and Kv 16-byte aligned).
