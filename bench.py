@@ -579,7 +579,7 @@ def run_serve(args):
         o.m_precise = args.m_precise
     if args.m_refine >= 0:
         o.m_refine = args.m_refine
-    o.max_iter = 100
+    o.max_iter = args.max_iter
     tol = 1e-6
     torch.cuda.synchronize()
     ab.svm_ipm_solve_batch([dict(X=p["X"], y=p["y"], C=p["C"], ell=p["sigma"], windows=p["windows"])
