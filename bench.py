@@ -46,7 +46,7 @@ def parse():
                          "independent problem per GPU")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="matvec", choices=["matvec", "ipm_batch", "serve", "precond_study", "predict",
-                                                                   "matvec_batch", "woodbury", "serve5"],
+                                                                   "matvec_batch", "woodbury", "serve5", "matvec64"],
                     help="matvec (default, the headline line) or ipm_batch (independent SVM "
                          "solves, one at a time vs concurrently)")
     ap.add_argument("--count", type=int, default=64, help="ipm_batch: number of problems")
@@ -862,6 +862,51 @@ def run_matvec_batch(args):
     return 0
 
 
+def run_matvec64(args):
+    """The FP64 plan's matvec (the precise path: N = 64, m = 6 unless --m-precise) on workload 3's
+    points (n = 1e5, four 3-D windows), one RHS, inputs resident, L2 flushed between steps; CUDA
+    events on the plan's stream, per-stage times from a second timed pass."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2312_00538_gb300 as ab
+    from synth import config3, matvec_vectors, SEED_BASE
+    cfg = config3()
+    X, W = cfg["X"], cfg["windows"]
+    n = X.shape[0]
+    m = args.m_precise or 6
+    plan = ab.anova_nfft_plan(X, W, 1.0, N=64, m=m, flags=ab.ANOVA_FP64)
+    v = torch.tensor(matvec_vectors(n, 1, SEED_BASE + 64)[:, 0], dtype=torch.float64, device="cuda")
+    kv = torch.empty_like(v)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        flush.zero_()
+        ab.anova_matvec(plan, v, kv, 1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st = torch.cuda.current_stream()
+    for a, b in ev:
+        flush.zero_()
+        a.record(st)
+        ab.anova_matvec(plan, v, kv, 1)
+        b.record(st)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ab.anova_plan_set_timing(plan, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ab.anova_matvec(plan, v, kv, 1)
+    stages, _ = ab.anova_plan_stage_times(plan)
+    line = {"metric": "ANOVA-NFFT FP64 matvec pts/s (workload 3 points)", "value": n / (ms / 1e3), "unit": "pts/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f64 (spread and interpolation sums in FP32 pairs)", "data": "synthetic",
+            "config": {"workload": "FP64 plan, n=%d, d=12, four 3-D windows, N=64, m=%d, 1 RHS" % (n, m),
+                       "l2": "flushed between steps"},
+            "stage_ms_per_step": {k: t / args.steps for k, t in stages.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_woodbury(args):
     """The Woodbury core M = I + L^T Theta^-1 L (Sec. 5) at workload-3 size (n = 1e5, rank 200):
     lowrank_precond_set_theta on the FP64 pipe against the exact-slice tensor-core path, Theta^-1
@@ -926,6 +971,8 @@ def main():
         return run_matvec_batch(args)
     if args.workload == "woodbury":
         return run_woodbury(args)
+    if args.workload == "matvec64":
+        return run_matvec64(args)
     if args.workload == "serve5":
         return run_serve5(args)
     if args.shard:

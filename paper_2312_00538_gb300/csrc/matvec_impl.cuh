@@ -6,6 +6,7 @@
 
 #include "conv_kernels.cuh"
 #include "nfft_kernels.cuh"
+#include "pair_kernels.cuh"
 
 namespace anova {
 
