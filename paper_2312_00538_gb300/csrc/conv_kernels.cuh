@@ -14,6 +14,7 @@
 #pragma once
 
 #include "kernels_common.cuh"
+#include "pair_arith.cuh"
 
 namespace anova {
 
@@ -146,19 +147,22 @@ struct ConvCfg {
     static constexpr size_t smem = sizeof(T) * ((size_t)LT * LS + NOS + NOS);
 };
 
-// Strides of window grids: element (u_0, .., u_{d-1}) at sum_k u_k n_os^{d-1-k}.
-template <typename T, int NOS, int DW, int LINES>
+// Strides of window grids: element (u_0, .., u_{d-1}) at sum_k u_k n_os^{d-1-k}. T is the grids'
+// element type, A the arithmetic type of the transforms (T, or pf pairs for FP64 grids; the
+// shared-memory layout is the same since sizeof(pf) == sizeof(double)).
+template <typename T, int NOS, int DW, int LINES, typename A = T>
 __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     pdl_wait();
     pdl_trigger();
+    static_assert(sizeof(A) == sizeof(T), "the arithmetic type takes the storage type's slots");
     using C = ConvCfg<T, NOS, LINES>;
     constexpr int VPL = NOS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LT = C::LT;
-    T *buf = reinterpret_cast<T *>(smem_raw);
-    T *twr = buf + LT * C::LS;
-    T *twi = twr + NOS / 2;
-    T *d1 = twi + NOS / 2;
+    A *buf = reinterpret_cast<A *>(smem_raw);
+    A *twr = buf + LT * C::LS;
+    A *twi = twr + NOS / 2;
+    A *d1 = twi + NOS / 2;
 
     const int ti = a.tile_begin + blockIdx.x;
     if (ti >= a.tile_end) return;
@@ -169,11 +173,11 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     const DevWindow dw = a.dwin[w];
 
     for (int i = threadIdx.x; i < NOS / 2; i += blockDim.x) {
-        twr[i] = reinterpret_cast<const T *>(a.tw)[2 * i];
-        twi[i] = reinterpret_cast<const T *>(a.tw)[2 * i + 1];
+        twr[i] = to_arith<A>(reinterpret_cast<const T *>(a.tw)[2 * i]);
+        twi[i] = to_arith<A>(reinterpret_cast<const T *>(a.tw)[2 * i + 1]);
     }
     for (int i = threadIdx.x; i < NOS; i += blockDim.x)
-        d1[i] = reinterpret_cast<const T *>(a.D1br)[((size_t)w * 3 + ax) * NOS + i];
+        d1[i] = to_arith<A>(reinterpret_cast<const T *>(a.D1br)[((size_t)w * 3 + ax) * NOS + i]);
 
     // axis stride, line stride (q) and outer stride (p)
     long long S[3] = {0, 0, 0};
@@ -204,19 +208,19 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
         if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % LT; u = i / LT; }
         T val = T(0);
         if (j < nlines) val = in[(long long)u * s_ax + (long long)(q0 + j) * s_q];
-        buf[j * C::LS + u] = val;
+        buf[j * C::LS + u] = to_arith<A>(val);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int pr = warp; pr < LT / 2; pr += blockDim.x / 32) {
         if (2 * pr >= nlines) break;
-        T re[VPL], im[VPL];
+        A re[VPL], im[VPL];
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             re[v] = buf[(2 * pr) * C::LS + 32 * v + lane];
             im[v] = buf[(2 * pr + 1) * C::LS + 32 * v + lane];
         }
-        conv_line<T, NOS>(re, im, twr, twi, d1, lane);
+        conv_line<A, NOS>(re, im, twr, twi, d1, lane);
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             buf[(2 * pr) * C::LS + 32 * v + lane] = re[v];
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a) {
     for (int i = threadIdx.x; i < LT * NOS; i += blockDim.x) {
         int j, u;
         if (s_ax == 1) { u = i % NOS; j = i / NOS; } else { j = i % LT; u = i / LT; }
-        if (j < nlines) out[(long long)u * s_ax + (long long)(q0 + j) * s_q] = buf[j * C::LS + u];
+        if (j < nlines) out[(long long)u * s_ax + (long long)(q0 + j) * s_q] = to_storage<T>(buf[j * C::LS + u]);
     }
 }
 

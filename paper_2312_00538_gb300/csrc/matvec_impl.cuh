@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "conv_kernels.cuh"
 #include "nfft_kernels.cuh"
@@ -81,10 +82,22 @@ cudaError_t launch_interp_t(const InterpArgs &a, int nseg, int nrhs, cudaStream_
     return launch_k(kern, dim3((nseg + NW - 1) / NW, nrhs), dim3(NW * 32), C::smem, st, a);
 }
 
+#ifndef ANOVA_F64_PAIR_FFT
+#define ANOVA_F64_PAIR_FFT 1  // FP64 grids: FFT passes in FP32 pairs
+#endif
+template <typename T>
+struct ConvArith {
+    using type = T;
+};
+template <>
+struct ConvArith<double> {
+    using type = std::conditional_t<ANOVA_F64_PAIR_FFT != 0, pf, double>;
+};
+
 template <typename T, int NOS, int DW, int LINES>
 cudaError_t launch_conv_t(const ConvArgs &a, int ntiles, int nrhs, cudaStream_t st) {
     using C = ConvCfg<T, NOS, LINES>;
-    auto kern = k_conv<T, NOS, DW, LINES>;
+    auto kern = k_conv<T, NOS, DW, LINES, typename ConvArith<T>::type>;
     static const cudaError_t configured =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (configured != cudaSuccess) return configured;
