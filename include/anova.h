@@ -119,7 +119,12 @@ anova_status anova_matvec(anova_plan_t plan, const void *v, void *Kv, int nrhs);
 /*
  * anova_matvec_host -- as anova_matvec with HOST buffers: copies v to the device, runs the
  * matvec and copies Kv back, then synchronises the plan's stream. Uses plan-owned staging
- * buffers (pinned host memory is faster but not required).
+ * buffers (pinned host memory is faster but not required). After a call the copy in, the
+ * matvec and the copy out are kept as one captured CUDA graph for the same (v_host, Kv_host,
+ * nrhs); a following call with those buffers launches the graph (same kernels, same results),
+ * any other call takes the stream path and captures again. The caller keeps the host buffers
+ * valid while the plan may still use them, as with any asynchronous copy. Not thread-safe with
+ * other calls on the same plan (as every plan call).
  */
 anova_status anova_matvec_host(anova_plan_t plan, const void *v_host, void *Kv_host, int nrhs);
 

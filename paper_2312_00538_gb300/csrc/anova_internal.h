@@ -167,6 +167,14 @@ struct anova_plan {
     // host-call staging
     void *dv = nullptr, *dkv = nullptr;
     int stage_rhs = 0;
+    // anova_matvec_host: the copy in, the matvec and the copy out captured as one graph for the
+    // buffers of the last call (rebuilt when they, nrhs or the workspace change)
+    cudaGraphExec_t host_exec = nullptr;
+    cudaStream_t host_cap = nullptr;   // private stream the graph is captured on
+    const void *host_v = nullptr;
+    void *host_kv = nullptr, *host_dv = nullptr;
+    int host_nrhs = 0;
+    uint64_t host_gen = 0;
 
     // optional per-stage CUDA-event timing (anova_plan_set_timing)
     struct StageEvt {

@@ -332,6 +332,8 @@ void destroy_plan(anova_plan *p) {
         if (p->join_evt[k]) cudaEventDestroy(p->join_evt[k]);
     }
     if (p->fork_evt) cudaEventDestroy(p->fork_evt);
+    if (p->host_exec) cudaGraphExecDestroy(p->host_exec);
+    if (p->host_cap) cudaStreamDestroy(p->host_cap);
     release_workspace(p);
     void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->chunks, p->wi_chunk, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
