@@ -1043,12 +1043,8 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
         k_cholesky<<<1, 1024, 0, st>>>(lr->M, r, lr->info, lr->dinv);
     }
     ANOVA_CUDA_TRY(cudaGetLastError());
-    int info = 0, tc_status = 0;
-    ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (tensor) ANOVA_CUDA_TRY(cudaMemcpyAsync(&tc_status, lr->tc_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
-    if (tc_status != 0) return fail(ANOVA_ERR_TIMEOUT, "a bounded tensor-core wait in the Woodbury core ran out");
-    if (info != 0) return fail(ANOVA_ERR_BREAKDOWN, "Woodbury core is not positive definite");
+    // the inverse factor and the Schur value are computed before the checks, so that one host
+    // synchronisation serves all three (a failed factor only yields values that are discarded)
     k_tri_inv<<<r, 32, sizeof(double) * r, st>>>(lr->M, lr->dinv, r, lr->Wl, lr->Wc);
     ANOVA_CUDA_TRY(cudaGetLastError());
     // Schur complement s = y^T A^{-1} y of the block preconditioner
@@ -1058,9 +1054,14 @@ anova_status lowrank_set_theta_impl(lowrank *lr, const double *theta, const doub
     k_dot_partial<<<nb, 256, 0, st>>>(y, lr->tmp, n, lr->dpart);
     k_sum_parts<<<1, 32, 0, st>>>(lr->dpart, nb, lr->schur);
     ANOVA_CUDA_TRY(cudaGetLastError());
+    int info = 0, tc_status = 0;
     double sv = 0.0;
+    ANOVA_CUDA_TRY(cudaMemcpyAsync(&info, lr->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (tensor) ANOVA_CUDA_TRY(cudaMemcpyAsync(&tc_status, lr->tc_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaMemcpyAsync(&sv, lr->schur, sizeof(double), cudaMemcpyDeviceToHost, st));
     ANOVA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tc_status != 0) return fail(ANOVA_ERR_TIMEOUT, "a bounded tensor-core wait in the Woodbury core ran out");
+    if (info != 0) return fail(ANOVA_ERR_BREAKDOWN, "Woodbury core is not positive definite");
     if (!(sv > 0.0) || !std::isfinite(sv)) return fail(ANOVA_ERR_BREAKDOWN, "y^T A^{-1} y is not positive");
     lr->schur_host = sv;
     lr->core_ready = true;
