@@ -50,7 +50,7 @@ struct Prec<double> {
 };
 
 #ifndef ANOVA_F64_PAIR
-#define ANOVA_F64_PAIR 1  // FP64 3-D spread: footprint sums in FP32 pairs
+#define ANOVA_F64_PAIR 1  // FP64 3-D spread and interpolation: multiply-adds in FP32 pairs
 #endif
 
 template <typename T, int DW, int M>

@@ -14,7 +14,9 @@ namespace anova {
 // all with explicitly rounded operations so that no contraction changes them. The window
 // weights are evaluated in FP64 as in k_spread and stored as pairs; tiles are pairs in shared
 // memory; the partial tile is written in FP64. Relative accuracy ~2^-44 of the sums of the terms'
-// magnitudes. Same work split and shared-memory layout as k_spread (DW = 3).
+// magnitudes. Same work split and shared-memory layout as k_spread (DW = 3). Cheaper than the
+// renormalised pair type of pair_arith.cuh (used by the FFT passes): a product is left as
+// (hi * hi, its error plus the cross terms) and only the accumulators' hi parts take the two-sum.
 struct fpair {
     float hi, lo;
 };
