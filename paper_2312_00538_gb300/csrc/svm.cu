@@ -16,6 +16,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/anova_svm.h"
@@ -905,28 +906,64 @@ anova_status svm_ipm_solve(const double *X, int64_t n, int d, const double *yh, 
                 for (int k = 0; k < 3 && 3 * l + k < d; ++k) W[3 * l + k] = 3 * l + k;
         }
         std::vector<double> ell(std::max(P, 1), o.ell);
-        anova_plan *p32 = nullptr, *p64 = nullptr;
+        // the FP32 plan, the FP64 plan and the refinement residuals' FP64 plan (same points and
+        // bandwidth, a shorter window); without tuning, the first and the last are built on helper
+        // threads while this thread builds the FP64 plan (their host work overlaps)
+        const bool sep_refine = o.m_refine != 0 && o.m_refine != o.m_precise;
+        auto build = [&](int N_, int m_, int prec, anova_plan **out) -> anova_status {
+            return o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, N_, m_, prec, o.cuda_stream, 1, 3,
+                                          nullptr, out)
+                              : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, N_, m_, prec, o.cuda_stream, out);
+        };
+        struct Helper {
+            anova_plan *plan = nullptr;
+            anova_status status = ANOVA_OK;
+            std::string error;
+            std::thread th;
+            ~Helper() {
+                if (th.joinable()) th.join();
+                if (plan) destroy_plan(plan);
+            }
+        } h32, h64r;
+        int dev = 0;
+        ANOVA_CUDA_TRY(cudaGetDevice(&dev));
+        auto start = [&](Helper &h, int N_, int m_, int prec) {
+            h.th = std::thread([&h, &build, dev, N_, m_, prec]() {
+                cudaSetDevice(dev);
+                h.status = build(N_, m_, prec, &h.plan);
+                if (h.status != ANOVA_OK) h.error = anova_last_error();
+            });
+        };
         anova_status s;
-        if ((s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32,
-                                        o.cuda_stream, 1, 3, nullptr, &p32)
-                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N, o.m, ANOVA_FP32,
-                                          o.cuda_stream, &p32)) != ANOVA_OK)
-            return s;
+        anova_plan *p64 = nullptr;
+        if (o.autotune) {
+            // tuned plans are timed one at a time
+            if ((s = build(o.N, o.m, ANOVA_FP32, &h32.plan)) != ANOVA_OK) return s;
+            if ((s = build(o.N_precise, o.m_precise, ANOVA_FP64, &p64)) != ANOVA_OK) return s;
+            if (sep_refine && (s = build(o.N_precise, o.m_refine, ANOVA_FP64, &h64r.plan)) != ANOVA_OK) {
+                destroy_plan(p64);
+                return s;
+            }
+        } else {
+            start(h32, o.N, o.m, ANOVA_FP32);
+            if (sep_refine) start(h64r, o.N_precise, o.m_refine, ANOVA_FP64);
+            s = build(o.N_precise, o.m_precise, ANOVA_FP64, &p64);
+            if (h32.th.joinable()) h32.th.join();
+            if (h64r.th.joinable()) h64r.th.join();
+            if (s != ANOVA_OK) return s;
+            for (Helper *h : {&h32, &h64r})
+                if (h->status != ANOVA_OK) {
+                    destroy_plan(p64);
+                    set_error(h->error);
+                    return h->status;
+                }
+        }
+        anova_plan *p32 = h32.plan;
+        h32.plan = nullptr;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g32(p32, destroy_plan);
-        if ((s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise,
-                                        ANOVA_FP64, o.cuda_stream, 1, 3, nullptr, &p64)
-                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_precise,
-                                          ANOVA_FP64, o.cuda_stream, &p64)) != ANOVA_OK)
-            return s;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64(p64, destroy_plan);
-        // the refinement residuals' FP64 plan: same points and bandwidth, a shorter window
-        anova_plan *p64r = p64;
-        if (o.m_refine != 0 && o.m_refine != o.m_precise &&
-            (s = o.autotune ? tune_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_refine,
-                                        ANOVA_FP64, o.cuda_stream, 1, 3, nullptr, &p64r)
-                            : create_plan(Xp, n, d, W.data(), P, ell.data(), nullptr, o.N_precise, o.m_refine,
-                                          ANOVA_FP64, o.cuda_stream, &p64r)) != ANOVA_OK)
-            return s;
+        anova_plan *p64r = sep_refine ? h64r.plan : p64;
+        h64r.plan = nullptr;
         std::unique_ptr<anova_plan, void (*)(anova_plan *)> g64r(p64r != p64 ? p64r : nullptr, destroy_plan);
         lowrank *lr = nullptr;
         if ((s = lowrank_build_impl(p64, o.precond, (int)std::min<int64_t>(o.rank, n), o.err_tol, o.seed, &lr)) != ANOVA_OK)
