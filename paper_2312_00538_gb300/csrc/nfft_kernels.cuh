@@ -541,14 +541,16 @@ struct BinReduceArgs {
     int tv_max;                  // largest tile volume among these bins (sets the chunk count)
 };
 
-// One CTA per (bin, chunk of 32 tile elements): warp k sums the work items k, k+8, k+16, ...
-// of its 32 elements, then warp 0 adds the eight partial sums in a fixed order.
-constexpr int kBinReduceChunk = 32;
+// One CTA per (bin, chunk of 128 tile elements): warp k sums the work items k, k+8, k+16, ... of
+// its chunk (four elements per lane, 32 apart, so four independent loads per item), then warps
+// 0-3 each add the eight partial sums of 32 elements in a fixed order.
+constexpr int kBinReduceChunk = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bin_reduce(BinReduceArgs a) {
     pdl_wait();
     pdl_trigger();
+    constexpr int EPL = kBinReduceChunk / 32;  // elements per lane
     __shared__ T part[8][kBinReduceChunk];
     const int chunks = (a.tv_max + kBinReduceChunk - 1) / kBinReduceChunk;
     const int b = a.mb_begin + blockIdx.x / chunks;
@@ -556,20 +558,31 @@ __global__ void __launch_bounds__(256) k_bin_reduce(BinReduceArgs a) {
     const int r = blockIdx.y;
     const int4 mb = a.mbins[b];
     const int tv = mb.z;
-    const int e = c * kBinReduceChunk + (threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
     const int slice = threadIdx.x >> 5;
+    const int e0 = c * kBinReduceChunk + lane;
     if (c * kBinReduceChunk >= tv) return;  // whole CTA: this bin's tile is shorter
     T *tiles = reinterpret_cast<T *>(a.tiles);
-    T s = T(0);
-    if (e < tv)
-        for (int k = slice; k < mb.y; k += 8) s += tiles[((size_t)(mb.x + k) * a.nrhs + r) * tv + e];
-    part[slice][threadIdx.x & 31] = s;
-    __syncthreads();
-    if (slice == 0 && e < tv) {
-        T t = part[0][threadIdx.x];
+    T s[EPL];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
-        tiles[((size_t)mb.x * a.nrhs + r) * tv + e] = t;
+    for (int i = 0; i < EPL; ++i) s[i] = T(0);
+    for (int k = slice; k < mb.y; k += 8) {
+        const T *tk = tiles + ((size_t)(mb.x + k) * a.nrhs + r) * tv;
+#pragma unroll
+        for (int i = 0; i < EPL; ++i)
+            if (e0 + 32 * i < tv) s[i] += tk[e0 + 32 * i];
+    }
+#pragma unroll
+    for (int i = 0; i < EPL; ++i) part[slice][lane + 32 * i] = s[i];
+    __syncthreads();
+    if (slice < EPL) {
+        const int e = e0 + 32 * slice;
+        if (e < tv) {
+            T t = part[0][lane + 32 * slice];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) t += part[k][lane + 32 * slice];
+            tiles[((size_t)mb.x * a.nrhs + r) * tv + e] = t;
+        }
     }
 }
 
