@@ -16,6 +16,7 @@ constexpr double kOversampling = 2.0;  // n_os = 2N
 constexpr double kEpsB = 0.1;          // kernel fit on |t| <= 1/2 - eps_B
 constexpr double kBoxHalf = 0.2;       // points in [-0.2, 0.2]
 constexpr int kSegMax = 256;           // points per segment (one cell, split at this size)
+constexpr int kSpreadSplit = 8;        // warps of the packed FP32 spread (cost-balanced point ranges)
 #ifndef ANOVA_WI_MAX
 #define ANOVA_WI_MAX 2048
 #endif
@@ -128,6 +129,7 @@ struct anova_plan {
                                   // consecutive points of one cell column of a work item,
                                   // {sorted start, count, l0 | l1 << 8 (column in the bin), 0}
     int *wi_chunk = nullptr;      // [nwi + 1]: work item x owns chunks [wi_chunk[x], wi_chunk[x + 1])
+    int *wsplit = nullptr;        // [nwi][kSpreadSplit + 1]: sorted-point ranges of the packed spread's warps
     int *wi_order = nullptr;      // per window: its work items by decreasing point count
     int *wi_gorder = nullptr;     // per dimension group: all its work items by decreasing point count
     int2 *bins = nullptr;         // per window per bin: {first work item, count}

@@ -566,6 +566,8 @@ anova_status matvec_windows(anova_plan *p, const T *v, int nrhs, int w0, int w1,
         const bool whole_group = a0 == gr.w_begin && a1 == gr.w_end;
         const int *order = whole_group && ANOVA_GROUP_ORDER ? p->wi_gorder : p->wi_order;
         sa.order = ANOVA_SPREAD_ORDER ? order : nullptr;
+        sa.wsplit = p->wsplit;
+        sa.wsplit_n = kSpreadSplit;
         if (wi1 > wi0) {
             cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nrhs, st);
             if (e != cudaSuccess) return cuda_fail(e, "spread launch");
@@ -709,6 +711,8 @@ anova_status grids_impl(anova_plan *p, const T *v, T *grids, int nrhs) {
             sa.wi_end = wi1;
             sa.wp = wp;
             sa.order = ANOVA_SPREAD_ORDER ? p->wi_order : nullptr;
+            sa.wsplit = p->wsplit;
+            sa.wsplit_n = kSpreadSplit;
             if (wi1 > wi0) {
                 cudaError_t e = dispatch_spread<T>(gr.dw, p->m, sa, wi1 - wi0, nr, p->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "spread launch");

@@ -44,6 +44,8 @@ struct SpreadArgs {
     int nrhs, wi_begin, wi_end;
     WinParams wp;
     const int *order;       // packed kernel: CTA k takes work item order[wi_begin + k] (null: identity)
+    const int *wsplit = nullptr;  // packed kernel: per work item, wsplit_n + 1 bounds of its warps'
+    int wsplit_n = 0;             // sorted-point ranges (null or a different warp count: equal points)
 };
 
 template <typename T, int DW, int M, int B, int NWARP>
@@ -334,14 +336,21 @@ __global__ void __launch_bounds__(NWARP * 32, ANOVA_SPREAD_MINB) k_spread3_x2(Sp
     __syncthreads();
     auto seg_at = [&](int i) -> int4 { return seg_cached ? segs_s[i - wi.y] : a.segs[i]; };
 
-    // each warp takes an equal share of the item's points (a cell may be split between two
-    // warps; each adds its part into its own tile)
-    const int4 s_first = seg_at(wi.y);
-    const int4 s_last = seg_at(wi.z - 1);
-    const int p0 = s_first.y, p1 = s_last.y + s_last.z;
-    const int len = p1 - p0;
-    const int pw0 = p0 + (int)(((long long)len * warp) / NWARP);
-    const int pw1 = p0 + (int)(((long long)len * (warp + 1)) / NWARP);
+    // each warp takes a contiguous share of the item's points, of about equal cost by the plan's
+    // split table (else of equal size); a cell may be split between two warps, each adds its
+    // part into its own tile
+    int pw0, pw1;
+    if (a.wsplit && a.wsplit_n == NWARP) {
+        pw0 = a.wsplit[(size_t)wi_idx * (NWARP + 1) + warp];
+        pw1 = a.wsplit[(size_t)wi_idx * (NWARP + 1) + warp + 1];
+    } else {
+        const int4 s_first = seg_at(wi.y);
+        const int4 s_last = seg_at(wi.z - 1);
+        const int p0 = s_first.y, p1 = s_last.y + s_last.z;
+        const int len = p1 - p0;
+        pw0 = p0 + (int)(((long long)len * warp) / NWARP);
+        pw1 = p0 + (int)(((long long)len * (warp + 1)) / NWARP);
+    }
 
     const float *fr0 = reinterpret_cast<const float *>(a.frac);
     const float *fr1 = fr0 + a.total, *fr2 = fr0 + 2 * a.total;

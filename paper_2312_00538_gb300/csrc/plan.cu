@@ -335,7 +335,7 @@ void destroy_plan(anova_plan *p) {
     if (p->host_exec) cudaGraphExecDestroy(p->host_exec);
     if (p->host_cap) cudaStreamDestroy(p->host_cap);
     release_workspace(p);
-    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->chunks, p->wi_chunk, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
+    void *bufs[] = {p->frac, p->xw, p->perm, p->cellloc, p->segs, p->wis, p->chunks, p->wi_chunk, p->wsplit, p->wi_order, p->wi_gorder, p->bins, p->mbins, p->ftiles, p->ftiles_full, p->dwin,
                     p->D1br, p->tw, p->dv, p->dkv, p->dev_status};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -745,6 +745,36 @@ anova_status create_plan_shaped(const double *points, int64_t n, int d, const in
         }
     }
     wi_chunk[wis.size()] = (int)chunks.size();
+    // point ranges of the packed FP32 spread's warps: each work item cut into kSpreadSplit
+    // contiguous ranges of about equal estimated cost. A warp pays per point (its footprint's
+    // multiply-adds, ~14 warp instructions), per batch of up to 32 points of one segment (the
+    // batch's window weights and staging, ~170) and per segment piece (adding the footprint
+    // into its tile, ~100), so a run of sparse cells costs more per point than a full cell; cut
+    // at equal point counts, the slowest warp of a work item averaged ~12 % above the mean.
+    std::vector<int> wsplit(wis.size() * (kSpreadSplit + 1));
+    for (size_t x = 0; x < wis.size(); ++x) {
+        const int4 t = wis[x];
+        int *o = &wsplit[x * (kSpreadSplit + 1)];
+        auto seg_cost = [](int sz) { return 14.0 * sz + 170.0 * ((sz + 31) / 32) + 100.0; };
+        double total_cost = 0.0;
+        for (int s2 = t.y; s2 < t.z; ++s2) total_cost += seg_cost(segs[s2].z);
+        o[0] = segs[t.y].y;
+        o[kSpreadSplit] = segs[t.z - 1].y + segs[t.z - 1].z;
+        int k = 1;
+        double acc = 0.0;
+        for (int s2 = t.y; s2 < t.z && k < kSpreadSplit; ++s2) {
+            const int sz = segs[s2].z;
+            const double c = seg_cost(sz);
+            while (k < kSpreadSplit && acc + c >= total_cost * k / kSpreadSplit) {
+                const double f = (total_cost * k / kSpreadSplit - acc) / c;
+                o[k] = segs[s2].y + (int)std::lround(std::min(1.0, std::max(0.0, f)) * sz);
+                ++k;
+            }
+            acc += c;
+        }
+        for (; k < kSpreadSplit; ++k) o[k] = o[kSpreadSplit];
+        for (k = 1; k <= kSpreadSplit; ++k) o[k] = std::max(o[k], o[k - 1]);
+    }
     p->nseg = (int)segs.size();
     p->nwi = (int)wis.size();
     p->ntiles = (int)ftiles.size();
@@ -835,6 +865,12 @@ anova_status create_plan_shaped(const double *points, int64_t n, int d, const in
                 q += ch.y;
             }
             if (q != (long long)segs[t.z - 1].y + segs[t.z - 1].z) return fail(ANOVA_ERR_CUDA, "plan check: chunk table");
+            // the warps' ranges start and end with the item's points and do not decrease
+            const int *o = &wsplit[x * (kSpreadSplit + 1)];
+            if (o[0] != segs[t.y].y || o[kSpreadSplit] != segs[t.z - 1].y + segs[t.z - 1].z)
+                return fail(ANOVA_ERR_CUDA, "plan check: spread split table");
+            for (int k = 1; k <= kSpreadSplit; ++k)
+                if (o[k] < o[k - 1]) return fail(ANOVA_ERR_CUDA, "plan check: spread split table");
         }
         for (const std::vector<int4> *tl : {&ftiles, &ftiles_full})
         for (const int4 &t : *tl) {
@@ -872,6 +908,7 @@ anova_status create_plan_shaped(const double *points, int64_t n, int d, const in
     if ((s = upload((void **)&p->wis, wis.data(), sizeof(int4) * wis.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->chunks, chunks.data(), sizeof(int4) * chunks.size())) != ANOVA_OK) return s;
     if ((s = upload((void **)&p->wi_chunk, wi_chunk.data(), sizeof(int) * wi_chunk.size())) != ANOVA_OK) return s;
+    if ((s = upload((void **)&p->wsplit, wsplit.data(), sizeof(int) * wsplit.size())) != ANOVA_OK) return s;
     {
         // each window's work items by decreasing point count (ties by index): persistent kernels
         // that take items in this order finish on the smallest ones
