@@ -11,6 +11,18 @@
 #include <new>
 #include <thread>
 
+// estimated warp instructions of the packed FP32 spread per point, per batch of up to 32 points of
+// one segment, and per segment piece: the weights of the cost-balanced warp shares
+#ifndef ANOVA_SPLIT_COST_POINT
+#define ANOVA_SPLIT_COST_POINT 14.0
+#endif
+#ifndef ANOVA_SPLIT_COST_BATCH
+#define ANOVA_SPLIT_COST_BATCH 170.0
+#endif
+#ifndef ANOVA_SPLIT_COST_PIECE
+#define ANOVA_SPLIT_COST_PIECE 100.0
+#endif
+
 #include "anova_internal.h"
 
 namespace anova {
@@ -755,7 +767,9 @@ anova_status create_plan_shaped(const double *points, int64_t n, int d, const in
     for (size_t x = 0; x < wis.size(); ++x) {
         const int4 t = wis[x];
         int *o = &wsplit[x * (kSpreadSplit + 1)];
-        auto seg_cost = [](int sz) { return 14.0 * sz + 170.0 * ((sz + 31) / 32) + 100.0; };
+        auto seg_cost = [](int sz) {
+            return ANOVA_SPLIT_COST_POINT * sz + ANOVA_SPLIT_COST_BATCH * ((sz + 31) / 32) + ANOVA_SPLIT_COST_PIECE;
+        };
         double total_cost = 0.0;
         for (int s2 = t.y; s2 < t.z; ++s2) total_cost += seg_cost(segs[s2].z);
         o[0] = segs[t.y].y;
