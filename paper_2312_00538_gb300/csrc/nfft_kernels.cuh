@@ -2,14 +2,15 @@
 // of the ANOVA fast summation (arXiv 2312.00538, Sec. 3: inner sum over i, outer sum over J).
 //
 // Points of every window are sorted by cell, cells grouped into bins of B^d cells. A spread
-// work item is a run of one bin's cells (at most kWiMax points). Each warp of the work item's
-// CTA accumulates its share of points cell by cell: lanes own rows of the (2M)^d footprint of
+// work item is a run of one bin's cells (at most the plan's work-item cap of points, 2048 by
+// default). Each warp of the work item's CTA accumulates a contiguous share of its points cell by
+// cell: lanes own rows of the (2M)^d footprint of
 // the current cell in registers, the window weights of 32 points at a time are staged in shared
 // memory and broadcast, and the footprint is added into the warp's own tile of the bin
 // neighbourhood ((B + 2M - 1)^d cells) -- no atomics anywhere. The CTA then sums its warp
-// tiles and writes one partial tile per work item; a reduction kernel adds the (at most 3^d
-// bins x work items) partial tiles covering each grid point in a fixed order, so the grid is
-// bit-for-bit reproducible.
+// tiles and writes one partial tile per work item; the bin reduction adds the partial tiles of
+// each bin, and the grid gather the (at most 3^d) bin tiles covering each grid point, both in a
+// fixed order, so the grid is bit-for-bit reproducible.
 #pragma once
 
 #include <type_traits>
@@ -284,11 +285,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_spread(SpreadArgs a) {
 
 // ------------------------------------------------------------------ FP32 3-D spread, packed
 // Specialisation of k_spread for FP32 3-D windows whose footprint edge 2M divides 16 (M = 2, 4):
-// a half-warp owns one point at a time, each lane holds 16/(2M) x ... rows (a, b) of the
-// footprint -- (2M)^2 / 16 rows of 2M values -- as f32x2 pairs along c, so the warp advances two
-// points per step with fma.rn.f32x2. The staged weights are laid out so that every load is a
-// 64- or 128-bit broadcast: X duplicated into pairs and permuted so that a lane's rows are
-// contiguous, Y duplicated into pairs, Z (times v) plain.
+// LPP lanes share a point (32, the default: the warp takes one point per step; 16: two points per
+// step), each lane holding (2M)^2 / LPP rows (a, b) of the footprint, 2M values each, as f32x2
+// pairs along c for fma.rn.f32x2. The staged weights are laid out so that every load is a
+// 32- to 128-bit broadcast: X permuted so that a lane's rows are contiguous, Y and Z (times v)
+// in order.
 template <int M, int B, int NWARP, int LPP = 16>
 struct SpreadX2Cfg {
     static constexpr int W2 = 2 * M;
