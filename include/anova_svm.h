@@ -255,6 +255,16 @@ anova_status svm_server_get_stats(svm_server_t server, svm_server_stats *stats);
  * solved with `opts` (NULL: defaults): both plans, the low-rank factor and the solver vectors.
  * Returns 0 for n < 1 or P < 1. */
 int64_t svm_request_footprint(int64_t n, int P, const svm_opts *opts);
+/* The workers' admission rule as a pure host function (no device work), for tests and for
+ * replaying a schedule. footprints[k] (bytes) and passed[k] (how many younger requests started
+ * ahead of it) describe the queued requests in arrival order; reserved_bytes is the estimate of
+ * the running requests and running their number. Stores in *pick the index of the request to
+ * start next, or -1 for none: the oldest when reserved_bytes + its footprint <= budget_bytes or
+ * running == 0; otherwise, if the oldest has been passed fewer than 4 times, the oldest younger
+ * request that fits; otherwise none. ANOVA_ERR_INVALID_ARG (and *pick = -1 where pick is not
+ * NULL) for a NULL pick, count < 0, or NULL arrays with count > 0. */
+anova_status svm_server_admission(const int64_t *footprints, const int32_t *passed, int count,
+                                  int64_t reserved_bytes, int64_t budget_bytes, int running, int *pick);
 /* Drains, stops the workers and frees the server. */
 void svm_server_destroy(svm_server_t server);
 

@@ -108,6 +108,7 @@ _SIGNATURES = {
     "svm_server_drain": (_c_int, [_vp]),
     "svm_server_get_stats": (_c_int, [_vp, _vp]),
     "svm_request_footprint": (_c_i64, [_c_i64, _c_int, _vp]),
+    "svm_server_admission": (_c_int, [_vp, _vp, _c_int, _c_i64, _c_i64, _c_int, _vp]),
     "svm_server_destroy": (None, [_vp]),
     "anova_last_error": (ctypes.c_char_p, []),
     "anova_version": (ctypes.c_char_p, []),
@@ -660,6 +661,19 @@ def _fill_problem(pr, X, y, C, ell, windows):
 def svm_request_footprint(n, P, opts=None):
     o = opts if opts is not None else svm_opts_default()
     return int(lib().svm_request_footprint(int(n), int(P), ctypes.byref(o)))
+
+
+def svm_server_admission(footprints, passed, reserved, budget, running):
+    """The server's admission rule (host only): index of the queued request to start next, or -1."""
+    fp = np.ascontiguousarray(footprints, dtype=np.int64)
+    ps = np.ascontiguousarray(passed, dtype=np.int32)
+    if fp.ndim != 1 or fp.shape != ps.shape:
+        raise ValueError("footprints and passed must be 1-D of equal length")
+    pick = ctypes.c_int(-1)
+    _check(lib().svm_server_admission(_ptr(fp, ctypes.c_int64) if fp.size else None,
+                                      _ptr(ps, ctypes.c_int32) if ps.size else None, int(fp.size),
+                                      int(reserved), int(budget), int(running), ctypes.byref(pick)))
+    return pick.value
 
 
 class SvmServer:

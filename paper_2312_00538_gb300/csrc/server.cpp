@@ -33,6 +33,22 @@ struct Request {
 // requests that do fit; after that nothing younger starts until it has started.
 constexpr int kMaxPass = 4;
 
+// The admission rule over `count` queued requests in arrival order (footprint(k), passed(k)):
+// the index of the request to start, or -1. The oldest starts once it fits the budget beside the
+// running requests, or when nothing runs (a request larger than the budget runs alone); while
+// it does not fit and has been passed fewer than kMaxPass times, the oldest younger request
+// that fits starts instead (backfill).
+template <class Footprint, class Passed>
+int admission_index(int count, Footprint footprint, Passed passed, int64_t reserved, int64_t budget,
+                    int64_t running) {
+    if (count <= 0) return -1;
+    if (reserved + footprint(0) <= budget || running == 0) return 0;
+    if (passed(0) >= kMaxPass) return -1;
+    for (int k = 1; k < count; ++k)
+        if (reserved + footprint(k) <= budget) return k;
+    return -1;
+}
+
 }  // namespace
 
 struct svm_server {
@@ -96,24 +112,14 @@ static void worker_loop(svm_server *s) {
         Request *req = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            // admission: the oldest request once it fits the budget (or nothing else is running);
-            // while it does not fit, the oldest younger request that fits may start instead
-            // (backfill), at most kMaxPass times past the same oldest request
+            // admission (admission_index): the oldest request once it fits the budget, else a
+            // younger one that fits (backfill), at most kMaxPass times past the same oldest one
             auto chosen = s->queue.end();
             auto pick = [&]() {
-                chosen = s->queue.end();
-                if (s->queue.empty()) return;
-                Request *head = s->queue.front();
-                if (s->reserved + head->footprint <= s->budget || s->running == 0) {
-                    chosen = s->queue.begin();
-                    return;
-                }
-                if (head->passed >= kMaxPass) return;
-                for (auto it = s->queue.begin() + 1; it != s->queue.end(); ++it)
-                    if (s->reserved + (*it)->footprint <= s->budget) {
-                        chosen = it;
-                        return;
-                    }
+                const int k = admission_index(
+                    (int)s->queue.size(), [&](int i) { return s->queue[i]->footprint; },
+                    [&](int i) { return s->queue[i]->passed; }, s->reserved, s->budget, s->running);
+                chosen = k < 0 ? s->queue.end() : s->queue.begin() + k;
             };
             s->cv_work.wait(lk, [&] {
                 if (s->stopping && s->queue.empty()) return true;
@@ -159,6 +165,18 @@ static void worker_loop(svm_server *s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+}
+
+anova_status svm_server_admission(const int64_t *footprints, const int32_t *passed, int count,
+                                  int64_t reserved_bytes, int64_t budget_bytes, int running, int *pick) {
+    if (!pick) return anova::fail(ANOVA_ERR_INVALID_ARG, "pick is NULL");
+    *pick = -1;
+    if (count < 0) return anova::fail(ANOVA_ERR_INVALID_ARG, "count must be >= 0");
+    if (count > 0 && (!footprints || !passed)) return anova::fail(ANOVA_ERR_INVALID_ARG, "NULL argument");
+    *pick = admission_index(
+        count, [&](int i) { return footprints[i]; }, [&](int i) { return (int)passed[i]; }, reserved_bytes,
+        budget_bytes, running);
+    return ANOVA_OK;
 }
 
 anova_status svm_server_create(const svm_opts *opts, double tol, int slots, int64_t hbm_budget_bytes,

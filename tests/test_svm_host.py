@@ -1,4 +1,5 @@
 """CPU-only checks of the solver ABI: Table 1 defaults (golden file) and argument validation."""
+import ctypes
 import json
 import os
 
@@ -106,3 +107,83 @@ def test_request_footprint_counts_transient_work(ab):
     tu = ab.svm_opts_default()
     tu.autotune = 1
     assert f(n, P, tu) > base
+
+
+def test_admission_rule_cases(ab):
+    """The workers' admission rule: the oldest request when it fits (or nothing runs), else the
+    oldest younger request that fits, until the oldest has been passed four times."""
+    f = ab.svm_server_admission
+    assert f([], [], 0, 100, 0) == -1                       # empty queue
+    assert f([60, 10], [0, 0], 30, 100, 1) == 0             # the oldest fits: FIFO
+    assert f([70, 10], [0, 0], 30, 100, 1) == 0             # exactly at the budget still fits
+    assert f([80, 10], [0, 0], 30, 100, 1) == 1             # backfill past the oldest
+    assert f([80, 90, 20, 10], [0, 0, 0, 0], 30, 100, 2) == 2   # the oldest younger that fits, not the smallest
+    assert f([80, 90, 75], [0, 0, 0], 30, 100, 1) == -1     # nothing fits
+    assert f([500, 10], [0, 0], 0, 100, 0) == 0             # larger than the budget: runs alone when idle
+    assert f([500, 10], [0, 0], 30, 100, 1) == 1
+    assert f([80, 10], [3, 0], 30, 100, 1) == 1             # passed 3 times: one more backfill
+    assert f([80, 10], [4, 0], 30, 100, 1) == -1            # passed 4 times: the rest waits for it
+    assert f([80, 10], [4, 0], 30, 100, 0) == 0
+    with pytest.raises(ValueError):
+        f([1, 2], [0], 0, 10, 0)
+    L = ab.lib()
+    pick = ctypes.c_int(7)
+    assert L.svm_server_admission(None, None, -1, 0, 10, 0, ctypes.byref(pick)) == ab.ANOVA_ERR_INVALID_ARG
+    assert pick.value == -1
+    assert L.svm_server_admission(None, None, 2, 0, 10, 0, ctypes.byref(pick)) == ab.ANOVA_ERR_INVALID_ARG
+    assert L.svm_server_admission(None, None, 0, 0, 10, 0, None) == ab.ANOVA_ERR_INVALID_ARG
+
+
+def test_admission_schedule_replay(ab):
+    """A replayed schedule (one slot per request up to four, unit-time steps): every request
+    starts, memory never exceeds the budget except for a request that runs alone, and no request
+    is passed more than four times. Checked against a plain restatement of the rule."""
+    rng = np.random.default_rng(2312)
+    budget, slots = 100, 4
+
+    def rule(fp, ps, reserved, running):
+        if not fp:
+            return -1
+        if reserved + fp[0] <= budget or running == 0:
+            return 0
+        if ps[0] >= 4:
+            return -1
+        for k in range(1, len(fp)):
+            if reserved + fp[k] <= budget:
+                return k
+        return -1
+
+    backfills, capped = 0, 0
+    for trial in range(20):
+        reqs = [(int(rng.integers(5, 130)), int(rng.integers(1, 6))) for _ in range(40)]
+        queue, running, t, started, max_passed = [], [], 0, 0, 0
+        arrivals = sorted(int(a) for a in rng.integers(0, 60, size=len(reqs)))
+        nxt = 0
+        while started < len(reqs):
+            while nxt < len(reqs) and arrivals[nxt] <= t:
+                queue.append([reqs[nxt][0], reqs[nxt][1], 0])
+                nxt += 1
+            running = [r for r in running if r[1] > t]
+            while len(running) < slots and queue:
+                reserved = sum(r[0] for r in running)
+                fp = [q[0] for q in queue]
+                ps = [q[2] for q in queue]
+                k = ab.svm_server_admission(fp, ps, reserved, budget, len(running))
+                assert k == rule(fp, ps, reserved, len(running))
+                if k < 0:
+                    # the bound at work: a younger request would fit but the oldest was passed 4 times
+                    if queue[0][2] >= 4 and any(reserved + q[0] <= budget for q in queue[1:]):
+                        capped += 1
+                    break
+                if k > 0:
+                    queue[0][2] += 1
+                    backfills += 1
+                q = queue.pop(k)
+                max_passed = max(max_passed, q[2])
+                running.append((q[0], t + q[1]))
+                started += 1
+                total = sum(r[0] for r in running)
+                assert total <= budget or len(running) == 1
+            t += 1
+        assert max_passed <= 4
+    assert backfills > 0 and capped > 0   # both branches of the rule were taken
