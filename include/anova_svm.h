@@ -268,6 +268,11 @@ anova_status svm_server_admission(const int64_t *footprints, const int32_t *pass
 /* Drains, stops the workers and frees the server. */
 void svm_server_destroy(svm_server_t server);
 
+/* sizeof of this ABI's structs by name: "anova_tune_report", "svm_opts", "svm_stats",
+ * "svm_problem", "svm_server_stats". A binding that mirrors their layouts can check its copies
+ * against these. Returns 0 for NULL or an unknown name. Host only. */
+int64_t anova_abi_struct_size(const char *name);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,7 @@ _SIGNATURES = {
     "svm_server_get_stats": (_c_int, [_vp, _vp]),
     "svm_request_footprint": (_c_i64, [_c_i64, _c_int, _vp]),
     "svm_server_admission": (_c_int, [_vp, _vp, _c_int, _c_i64, _c_i64, _c_int, _vp]),
+    "anova_abi_struct_size": (_c_i64, [ctypes.c_char_p]),
     "svm_server_destroy": (None, [_vp]),
     "anova_last_error": (ctypes.c_char_p, []),
     "anova_version": (ctypes.c_char_p, []),

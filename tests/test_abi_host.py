@@ -114,3 +114,17 @@ def test_unused_features_may_lie_outside_the_box(ab):
         ab.anova_nfft_plan(X, [[0, 1, 2]], 1.0)
     except ab.AnovaError as e:
         assert e.status == ab.ANOVA_ERR_CUDA
+
+
+def test_struct_layouts_match_the_headers(ab):
+    """The binding's ctypes mirrors of the ABI structs have the C sizes (a field added on one side
+    only would shift every later field)."""
+    L = ctypes.CDLL(ab.LIB_PATH)
+    L.anova_abi_struct_size.restype = ctypes.c_int64
+    L.anova_abi_struct_size.argtypes = [ctypes.c_char_p]
+    for name in ["anova_tune_report", "svm_opts", "svm_stats", "svm_problem", "svm_server_stats"]:
+        c_size = L.anova_abi_struct_size(name.encode())
+        assert c_size > 0, name
+        assert ctypes.sizeof(getattr(ab, name)) == c_size, name
+    assert L.anova_abi_struct_size(b"no_such_struct") == 0
+    assert L.anova_abi_struct_size(None) == 0
